@@ -1,0 +1,394 @@
+"""CPU FP64 oracle for the OCP-QP primal-dual interior-point method.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import this
+module: only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` use it.  It shares no code with the CUDA solver.
+
+What it computes, and the passages it follows (HPIPM paper, arXiv 2003.02547):
+
+* ``assemble``      -- the OCP QP of Sec. 2.2 written out as the generic QP of
+                       Sec. 3.1, eq. (qp):  min 1/2 y'Hy + g'y  s.t.  Ay = b,
+                       Cy >= d.  Stage variables are y_n = [u_n; x_n].
+* ``residuals``     -- the residual function of eq. (delta) (r_g, r_b, r_d, r_m)
+                       with the Lagrangian sign convention of Sec. 3.1.
+* ``newton_step``   -- eq. (delta) solved by eliminating dt then dlam (Sec. 3.3)
+                       and solving the reduced KKT system eq. (kkt) with a dense
+                       symmetric-indefinite LDL^T (LAPACK ?sytrf/?sytrs), or a
+                       sparse LU for large systems.  No Riccati recursion.
+* ``solve``         -- the infeasible-start Mehrotra predictor-corrector of
+                       Sec. 4.2 in the delta formulation (Sec. 3.2, mode
+                       'speed'), with the conditional corrector, the lower
+                       clamp on lambda and t, and warm start (Sec. 4.2).
+
+Conventions (fixed here, shared by the CUDA path through the C header, not
+through code):
+
+* Equality rows: for n = 0..N-1, -B_n u_n - A_n x_n + x_{n+1} = b_n, so that
+  r_b = -A y + b = A_n x_n + B_n u_n + b_n - x_{n+1} and the multiplier
+  pi_{n+1} of that block is the gradient of the cost-to-go at x_{n+1}.
+* Inequalities: every two-sided constraint lo <= c(y) <= hi gives a lower
+  side c(y) - lo >= 0 and an upper side hi - c(y) >= 0.  Per stage the
+  constraint list is [box on u (idxbu order); box on x (idxbx order);
+  general rows D u + C x], nc_n entries, and lambda/t hold the nc_n lower
+  sides followed by the nc_n upper sides.  A side with an infinite bound is
+  masked: it is left out of the arithmetic and reported as lambda = 0, t = 1.
+
+Readings where the paper is silent (the same in the CUDA path):
+
+* start: y = 0, pi = 0, lambda = 1, t = max(1, c(y) - bound) per side;
+* centring sigma = (mu_aff / mu)^3 (Mehrotra's heuristic);
+* conditional corrector: keep it if mu after its step <= corr_k * mu_aff,
+  otherwise take the predictor-centring direction (r_m = lambda t - sigma mu);
+* step alpha = min(1, tau_b * alpha_max), tau_b = 0.995; the predictor
+  uses alpha_aff = min(1, alpha_max);
+* after each step lambda >= lam_min and t >= t_min (1e-16 by default);
+* exit when ||r_g||inf <= tol_stat, ||r_b||inf <= tol_eq, ||r_d||inf <= tol_ineq
+  and mu <= tol_comp (unscaled infinity norms), or at iter_max, or when the
+  step falls below alpha_min.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+import scipy.linalg
+import scipy.sparse
+import scipy.sparse.linalg
+
+CONVERGED, MAX_ITER, MIN_STEP, NAN_FOUND = 0, 1, 2, 3
+
+DENSE_MAX = 1500   # reduced-KKT dimension up to which the dense LDL^T is used
+
+
+@dataclass
+class IpmArg:
+    iter_max: int = 100
+    tol_stat: float = 1e-10
+    tol_eq: float = 1e-10
+    tol_ineq: float = 1e-10
+    tol_comp: float = 1e-10
+    alpha_min: float = 1e-12
+    lam_min: float = 1e-16
+    t_min: float = 1e-16
+    tau_b: float = 0.995
+    corr_k: float = 2.0
+    cond_corr: bool = True
+    warm_start: int = 0        # 0 none, 1 primal (y, pi), 2 primal + dual
+    warm_min: float = 1e-2     # lower clamp for warm-started lambda and t
+    force_dense: Optional[bool] = None
+
+
+@dataclass
+class DenseQp:
+    """Generic-QP form of one OCP QP (Sec. 3.1, eq. qp)."""
+    H: np.ndarray
+    g: np.ndarray
+    A: np.ndarray
+    b: np.ndarray
+    C: np.ndarray          # active sides only
+    d: np.ndarray
+    active: np.ndarray     # bool mask over the full side layout
+    ny: int
+    neq: int
+    nside: int             # full side count, masked sides included
+    var_off: list = field(default_factory=list)
+    eq_off: list = field(default_factory=list)
+    side_off: list = field(default_factory=list)
+
+
+def assemble(qp) -> DenseQp:
+    """Write the stage-wise OCP QP (Sec. 2.2) as one dense generic QP."""
+    N = qp.N
+    nv = [qp.nx[n] + qp.nu[n] for n in range(N + 1)]
+    var_off = np.concatenate([[0], np.cumsum(nv)]).astype(int)
+    ny = int(var_off[-1])
+    eq_sz = [qp.nx[n + 1] for n in range(N)]
+    eq_off = np.concatenate([[0], np.cumsum(eq_sz)]).astype(int)
+    neq = int(eq_off[-1])
+    nc = [qp.nbu(n) + qp.nbx(n) + qp.ng(n) for n in range(N + 1)]
+    side_off = np.concatenate([[0], np.cumsum([2 * c for c in nc])]).astype(int)
+    nside = int(side_off[-1])
+
+    H = np.zeros((ny, ny))
+    g = np.zeros(ny)
+    for n in range(N + 1):
+        o, nu, nx = var_off[n], qp.nu[n], qp.nx[n]
+        H[o:o + nu, o:o + nu] = qp.R[n]
+        H[o:o + nu, o + nu:o + nu + nx] = qp.S[n]
+        H[o + nu:o + nu + nx, o:o + nu] = qp.S[n].T
+        H[o + nu:o + nu + nx, o + nu:o + nu + nx] = qp.Q[n]
+        g[o:o + nu] = qp.r[n]
+        g[o + nu:o + nu + nx] = qp.q[n]
+
+    A = np.zeros((neq, ny))
+    b = np.zeros(neq)
+    for n in range(N):
+        rows = slice(eq_off[n], eq_off[n + 1])
+        o, nu, nx = var_off[n], qp.nu[n], qp.nx[n]
+        A[rows, o:o + nu] = -qp.B[n]
+        A[rows, o + nu:o + nu + nx] = -qp.A[n]
+        o1, nu1, nx1 = var_off[n + 1], qp.nu[n + 1], qp.nx[n + 1]
+        A[rows, o1 + nu1:o1 + nu1 + nx1] = np.eye(nx1)
+        b[rows] = qp.b[n]
+
+    Crow = np.zeros((nside, ny))
+    dfull = np.zeros(nside)
+    active = np.zeros(nside, dtype=bool)
+    for n in range(N + 1):
+        o, nu = var_off[n], qp.nu[n]
+        rows = []
+        lo = []
+        hi = []
+        for k, i in enumerate(qp.idxbu[n]):
+            r = np.zeros(ny)
+            r[o + int(i)] = 1.0
+            rows.append(r)
+            lo.append(qp.lbu[n][k])
+            hi.append(qp.ubu[n][k])
+        for k, i in enumerate(qp.idxbx[n]):
+            r = np.zeros(ny)
+            r[o + nu + int(i)] = 1.0
+            rows.append(r)
+            lo.append(qp.lbx[n][k])
+            hi.append(qp.ubx[n][k])
+        for k in range(qp.ng(n)):
+            r = np.zeros(ny)
+            r[o:o + nu] = qp.D[n][k]
+            r[o + nu:o + nu + qp.nx[n]] = qp.C[n][k]
+            rows.append(r)
+            lo.append(qp.lg[n][k])
+            hi.append(qp.ug[n][k])
+        c = len(rows)
+        s = side_off[n]
+        for k in range(c):
+            # lower side: c(y) - lo >= 0 ; upper side: -c(y) + hi >= 0
+            Crow[s + k] = rows[k]
+            dfull[s + k] = lo[k]
+            active[s + k] = np.isfinite(lo[k])
+            Crow[s + c + k] = -rows[k]
+            dfull[s + c + k] = -hi[k]
+            active[s + c + k] = np.isfinite(hi[k])
+    return DenseQp(H=H, g=g, A=A, b=b, C=Crow[active], d=dfull[active], active=active,
+                   ny=ny, neq=neq, nside=nside, var_off=list(var_off),
+                   eq_off=list(eq_off), side_off=list(side_off))
+
+
+def residuals(dq: DenseQp, y, pi, lam, t):
+    """Residual function of eq. (delta): r_g, r_b, r_d (active sides) and
+    the duality measure mu = lam't / n_c."""
+    rg = dq.H @ y + dq.g - dq.A.T @ pi - dq.C.T @ lam
+    rb = -dq.A @ y + dq.b
+    rd = -dq.C @ y + dq.d + t
+    nc = lam.size
+    mu = float(lam @ t) / nc if nc else 0.0
+    return rg, rb, rd, mu
+
+
+class KktFactor:
+    """Factorisation of the reduced KKT matrix of eq. (kkt) at fixed (lam, t)."""
+
+    def __init__(self, dq: DenseQp, lam, t, force_dense: Optional[bool] = None):
+        self.dq = dq
+        self.lam = lam
+        self.t = t
+        W = lam / t
+        Ht = dq.H + dq.C.T @ (W[:, None] * dq.C)
+        n = dq.ny + dq.neq
+        self.n = n
+        dense = (n <= DENSE_MAX) if force_dense is None else force_dense
+        self.dense = dense
+        if dense:
+            K = np.zeros((n, n))
+            K[:dq.ny, :dq.ny] = Ht
+            K[:dq.ny, dq.ny:] = -dq.A.T
+            K[dq.ny:, :dq.ny] = -dq.A
+            # symmetric-indefinite LDL^T (Bunch-Kaufman), LAPACK dsytrf
+            lu, ipiv, info = scipy.linalg.lapack.dsytrf(K, lower=1)
+            if info != 0:
+                raise np.linalg.LinAlgError(f"dsytrf info={info}")
+            self.lu, self.ipiv = lu, ipiv
+        else:
+            Ks = scipy.sparse.bmat([[scipy.sparse.csc_matrix(Ht), scipy.sparse.csc_matrix(-dq.A.T)],
+                                    [scipy.sparse.csc_matrix(-dq.A), None]], format="csc")
+            self.splu = scipy.sparse.linalg.splu(Ks)
+
+    def solve_reduced(self, rhs):
+        if self.dense:
+            x, info = scipy.linalg.lapack.dsytrs(self.lu, self.ipiv, rhs, lower=1)
+            if info != 0:
+                raise np.linalg.LinAlgError(f"dsytrs info={info}")
+            return x
+        return self.splu.solve(rhs)
+
+    def step(self, rg, rb, rd, rm):
+        """Newton step of eq. (delta): eliminate dt = C dy - r_d and
+        dlam = -T^{-1}(r_m + Lam dt) (Sec. 3.3), solve eq. (kkt) for (dy, dpi)."""
+        dq, lam, t = self.dq, self.lam, self.t
+        W = lam / t
+        gt = rg - dq.C.T @ (W * rd - rm / t)
+        rhs = -np.concatenate([gt, rb])
+        sol = self.solve_reduced(rhs)
+        dy = sol[:dq.ny]
+        dpi = sol[dq.ny:]
+        dt = dq.C @ dy - rd
+        dlam = -(rm + lam * dt) / t
+        return dy, dpi, dlam, dt
+
+
+def newton_step(dq: DenseQp, y, pi, lam, t, sigma_mu: float = 0.0, force_dense=None):
+    """One Newton direction of eq. (delta) at the given iterate with
+    r_m = lam*t - sigma_mu (sigma_mu = 0: affine predictor)."""
+    rg, rb, rd, _ = residuals(dq, y, pi, lam, t)
+    rm = lam * t - sigma_mu
+    return KktFactor(dq, lam, t, force_dense).step(rg, rb, rd, rm)
+
+
+def _max_step(lam, t, dlam, dt) -> float:
+    """Largest alpha >= 0 with lam + alpha dlam >= 0 and t + alpha dt >= 0
+    (inf when no component decreases)."""
+    a = np.inf
+    neg = dlam < 0
+    if np.any(neg):
+        a = min(a, float(np.min(-lam[neg] / dlam[neg])))
+    neg = dt < 0
+    if np.any(neg):
+        a = min(a, float(np.min(-t[neg] / dt[neg])))
+    return a
+
+
+@dataclass
+class IpmResult:
+    y: np.ndarray
+    pi: np.ndarray
+    lam: np.ndarray        # full side layout (masked sides 0)
+    t: np.ndarray          # full side layout (masked sides 1)
+    status: int
+    iters: int
+    res: tuple             # (||r_g||inf, ||r_b||inf, ||r_d||inf, mu) at exit
+    history: list = field(default_factory=list)
+    dq: Optional[DenseQp] = None
+
+
+def initial_point(dq: DenseQp, y=None, pi=None, lam=None, t=None, arg: IpmArg = IpmArg()):
+    """Start point (reading: y = 0, pi = 0, lam = 1, t = max(1, Cy - d));
+    warm start 1 keeps the given (y, pi), warm start 2 also the given
+    (lam, t) clamped below by warm_min (Sec. 4.2: warm start of the primal,
+    or of the primal and dual variables)."""
+    if arg.warm_start >= 1 and y is not None:
+        y = np.array(y, dtype=np.float64)
+        pi = np.zeros(dq.neq) if pi is None else np.array(pi, dtype=np.float64)
+    else:
+        y = np.zeros(dq.ny)
+        pi = np.zeros(dq.neq)
+    if arg.warm_start >= 2 and lam is not None and t is not None:
+        lam = np.maximum(np.asarray(lam, dtype=np.float64)[dq.active], arg.warm_min)
+        t = np.maximum(np.asarray(t, dtype=np.float64)[dq.active], arg.warm_min)
+    else:
+        lam = np.ones(dq.C.shape[0])
+        t = np.maximum(1.0, dq.C @ y - dq.d)
+    return y, pi, lam, t
+
+
+def expand_sides(dq: DenseQp, v, fill):
+    out = np.full(dq.nside, fill, dtype=np.float64)
+    out[dq.active] = v
+    return out
+
+
+def solve(qp, arg: IpmArg = IpmArg(), y0=None, pi0=None, lam0=None, t0=None,
+          dq: Optional[DenseQp] = None, record: bool = False) -> IpmResult:
+    """Infeasible-start Mehrotra predictor-corrector IPM (Sec. 4.2) in the
+    delta formulation (Sec. 3.2), residual-based exit (mode 'speed')."""
+    if dq is None:
+        dq = assemble(qp)
+    y, pi, lam, t = initial_point(dq, y0, pi0, lam0, t0, arg)
+    nc = lam.size
+    status = MAX_ITER
+    it = 0
+    alpha = 1.0
+    hist = []
+    while True:
+        rg, rb, rd, mu = residuals(dq, y, pi, lam, t)
+        res = (np.max(np.abs(rg), initial=0.0), np.max(np.abs(rb), initial=0.0),
+               np.max(np.abs(rd), initial=0.0), mu)
+        if record:
+            hist.append(dict(y=y.copy(), pi=pi.copy(), lam=lam.copy(), t=t.copy(), res=res, alpha=alpha))
+        if not all(np.isfinite(res)):
+            status = NAN_FOUND
+            break
+        if (res[0] <= arg.tol_stat and res[1] <= arg.tol_eq and res[2] <= arg.tol_ineq
+                and res[3] <= arg.tol_comp):
+            status = CONVERGED
+            break
+        if it >= arg.iter_max:
+            status = MAX_ITER
+            break
+        if it > 0 and alpha < arg.alpha_min:
+            status = MIN_STEP
+            break
+        fac = KktFactor(dq, lam, t, arg.force_dense)
+        # predictor (affine) direction: r_m = lam * t
+        rm = lam * t
+        dy, dpi, dlam, dt = fac.step(rg, rb, rd, rm)
+        if nc:
+            a_aff = min(1.0, _max_step(lam, t, dlam, dt))
+            mu_aff = float((lam + a_aff * dlam) @ (t + a_aff * dt)) / nc
+            sigma = (mu_aff / mu) ** 3 if mu > 0 else 0.0
+            # Mehrotra corrector: second-order term and centring
+            rm_c = lam * t + dlam * dt - sigma * mu
+            cdy, cdpi, cdlam, cdt = fac.step(rg, rb, rd, rm_c)
+            use_corr = True
+            if arg.cond_corr:
+                a_c = min(1.0, _max_step(lam, t, cdlam, cdt))
+                mu_c = float((lam + a_c * cdlam) @ (t + a_c * cdt)) / nc
+                use_corr = mu_c <= arg.corr_k * mu_aff
+            if use_corr:
+                dy, dpi, dlam, dt = cdy, cdpi, cdlam, cdt
+            else:
+                rm_pc = lam * t - sigma * mu
+                dy, dpi, dlam, dt = fac.step(rg, rb, rd, rm_pc)
+            alpha = min(1.0, arg.tau_b * _max_step(lam, t, dlam, dt))
+        else:
+            alpha = 1.0
+        y = y + alpha * dy
+        pi = pi + alpha * dpi
+        lam = np.maximum(lam + alpha * dlam, arg.lam_min)
+        t = np.maximum(t + alpha * dt, arg.t_min)
+        it += 1
+    return IpmResult(y=y, pi=pi, lam=expand_sides(dq, lam, 0.0), t=expand_sides(dq, t, 1.0),
+                     status=status, iters=it, res=res, history=hist, dq=dq)
+
+
+def full_residuals(qp, y, pi, lam_full, t_full, dq: Optional[DenseQp] = None):
+    """KKT residual norms of a candidate solution given in the full side
+    layout: (||r_g||inf, ||r_b||inf, ||r_d||inf, mu, max_i lam_i t_i)."""
+    if dq is None:
+        dq = assemble(qp)
+    lam = np.asarray(lam_full)[dq.active]
+    t = np.asarray(t_full)[dq.active]
+    rg, rb, rd, mu = residuals(dq, np.asarray(y), np.asarray(pi), lam, t)
+    mx = float(np.max(lam * t)) if lam.size else 0.0
+    return (float(np.max(np.abs(rg), initial=0.0)), float(np.max(np.abs(rb), initial=0.0)),
+            float(np.max(np.abs(rd), initial=0.0)), mu, mx)
+
+
+def objective(dq: DenseQp, y) -> float:
+    return 0.5 * float(y @ dq.H @ y) + float(dq.g @ y)
+
+
+def duality_gap(dq: DenseQp, y, pi, lam_act) -> float:
+    """Primal objective minus the Lagrangian dual objective
+    -1/2 y'Hy + b'pi + d'lam (valid where Hy + g - A'pi - C'lam = 0)."""
+    dual = -0.5 * float(y @ dq.H @ y) + float(dq.b @ pi) + float(dq.d @ lam_act)
+    return objective(dq, y) - dual
+
+
+def split_stages(qp, dq: DenseQp, y):
+    """y -> list of (u_n, x_n)."""
+    out = []
+    for n in range(qp.N + 1):
+        o = dq.var_off[n]
+        nu, nx = qp.nu[n], qp.nx[n]
+        out.append((y[o:o + nu], y[o + nu:o + nu + nx]))
+    return out
