@@ -1,0 +1,375 @@
+"""Benchmark: batched OCP-QP IPM solves per second on GB300.
+
+Workload (one "step"): the mass-spring chain of Sec. 5.1 with 8 masses
+(nx = 16, nu = 7), N = 30, Q = I, R = I, |u| <= 0.5, |x| <= 4; a batch of
+1024 QPs that differ only in x0 ~ U[-1, 1]^16, each solved to KKT residual
+1e-8 by the mixed-precision IPM (FP32 Riccati factor/solve, FP64 residuals,
+refinement, step length and duality measure) in one kernel launch.
+
+JSON line fields follow the driver contract; see the design doc for the roofline
+arithmetic.  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "QP solves/s to KKT res 1e-8 (mixed+batched vs plain FP64 GPU IPM); p50/p99 ms"
+UNIT = "QP/s"
+BATCH = 1024
+HORIZON = 30
+MASSES = 8
+WORKLOAD = "mass-spring chain M=8 (nx=16, nu=7), N=30, batch 1024, x0~U[-1,1]"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gq", choices=["gq", "reference"])
+    p.add_argument("--batch", type=int, default=BATCH)
+    p.add_argument("--plain-sample", type=int, default=64,
+                   help="QPs solved one launch each for the plain FP64 GPU baseline")
+    p.add_argument("--cpu-sample", type=int, default=48, help="QPs in the oracle CPU baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# flop model (algorithmic work per QP)
+# ----------------------------------------------------------------------------
+def qp_flops(qp):
+    """(factorisation, one Riccati solve, one residual evaluation) flops."""
+    f = s = r = 0.0
+    for n in range(qp.N + 1):
+        nv = qp.nx[n] + qp.nu[n]
+        nx1 = qp.nx[n + 1] if n < qp.N else 0
+        ng = qp.ng(n)
+        f += nx1 * nx1 * nv + nx1 * nv * nv + nv ** 3 / 3.0 + ng * nv * nv
+        s += 2.0 * (nv * nv + 2.0 * nx1 * nv)
+        r += 2.0 * (nv * nv + 2.0 * nx1 * nv + 2.0 * ng * nv)
+    return f, s, r
+
+
+def work_split(qps, stats):
+    """Algorithmic flops of one batch solve split by arithmetic type."""
+    f32 = f64 = 0.0
+    for qp, st in zip(qps, stats):
+        f, s, r = qp_flops(qp)
+        nf = int(st["n_fact"])
+        nf64 = int(st["n_fact64"])
+        frac64 = nf64 / nf if nf else 0.0
+        ns = int(st["n_solve"])
+        f64 += nf64 * f + ns * s * frac64 + int(st["n_res"]) * r
+        f32 += (nf - nf64) * f + ns * s * (1.0 - frac64)
+    return f32, f64
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle baseline
+# ----------------------------------------------------------------------------
+def _oracle_worker(indices):
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import ocp_ipm as O
+    from paper_2003_02547_gb300 import workloads as W
+    ok = 0
+    for i in indices:
+        r = O.solve(W.mass_spring_qp(i, M=MASSES, N=HORIZON), O.IpmArg(tol_stat=1e-8, tol_eq=1e-8,
+                                                                        tol_ineq=1e-8, tol_comp=1e-8))
+        ok += r.status == O.CONVERGED
+    return ok
+
+
+def cpu_oracle(sample: int, offset: int = 0):
+    """Solve `sample` QPs of the workload with the CPU oracle on a spawn pool
+    of single-threaded workers over the host cores; returns (QP/s, cores)."""
+    import multiprocessing as mp
+    cores = min(os.cpu_count() or 1, 64, sample)
+    env_keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        chunks = [list(range(offset + c, offset + sample, cores)) for c in range(cores)]
+        with ctx.Pool(cores) as pool:
+            pool.map(_oracle_worker, [[offset]] * cores)   # import + warm the workers
+            t0 = time.perf_counter()
+            ok = sum(pool.map(_oracle_worker, chunks))
+            dt = time.perf_counter() - t0
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return sample / dt, cores, ok, dt
+
+
+# ----------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reference_arm(a):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    sample = max(4, min(a.cpu_sample, 64))
+    vals = []
+    cores = 1
+    for k in range(a.warmup + a.steps):
+        v, cores, ok, dt = cpu_oracle(sample, offset=k * sample % BATCH)
+        if k >= a.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sample / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": BATCH, "horizon": HORIZON, "nx": 16, "nu": 7,
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} QPs of the workload per step (spawn pool, 1 thread/worker)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return reference_arm(a)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+
+    # CPU baseline first (spawn pool; no GPU state is inherited)
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        v, cores, ok, dt = cpu_oracle(a.cpu_sample)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"first {a.cpu_sample} QPs of the workload ({dt:.1f} s wall, {ok} converged)"}
+
+    from paper_2003_02547_gb300 import build, gq, workloads as W
+    from paper_2003_02547_gb300.batch import QpBatch
+    build.build()
+
+    qps = [W.mass_spring_qp(rank * a.batch + i, M=MASSES, N=HORIZON) for i in range(a.batch)]
+    b = QpBatch(qps, device=dev)
+    arg_mixed = gq.default_arg(gq.MODE_SPEED, gq.PREC_MIXED)
+    arg_fp64 = gq.default_arg(gq.MODE_SPEED, gq.PREC_FP64)
+    stream = torch.cuda.current_stream()
+    b.upload()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- device-timed batched mixed solves ----------------
+    for _ in range(a.warmup):
+        flush.zero_()
+        b.solve(arg_mixed)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    barrier()
+    for e0, e1 in evs:
+        flush.zero_()                       # L2 flush between timed steps, outside the events
+        e0.record(stream)
+        b.solve(arg_mixed)
+        e1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    launches = a.steps                      # one IPM kernel launch per step
+    b.download()
+    torch.cuda.synchronize()
+    st = b.all_stats()
+    conv = int(np.sum(st["status"] == 0))
+    fallback = int(np.sum(st["flags"] & gq.FLAG_FP64_FALLBACK != 0))
+    mean_ms = statistics.mean(step_ms)
+    tmax = torch.tensor([mean_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    mean_ms_max = float(tmax.item())
+    value = world * a.batch / (mean_ms_max * 1e-3)
+    step_sorted = sorted(step_ms)
+    p50 = float(np.percentile(step_sorted, 50))
+    p99 = float(np.percentile(step_sorted, 99))
+
+    # ---------------- roofline of the IPM kernel ----------------
+    f32, f64 = work_split(qps, st)
+    P32 = 152 * 128 * 2 * 2.07e9          # FP32 FMA lanes x 2 x max SM clock
+    P64 = 1.25e12                          # nominal GB300 FP64 rate
+    t_kernel = mean_ms * 1e-3
+    t_min = f32 / P32 + f64 / P64
+    achieved = (f32 + f64) / t_kernel
+    peak_eff = (f32 + f64) / t_min if t_min > 0 else float("nan")
+
+    # ---------------- e2e through the C ABI with host buffers ----------------
+    for _ in range(2):
+        b.upload()
+        b.solve(arg_mixed)
+        b.download()
+    barrier()
+    e2e_ms = []
+    for _ in range(max(3, a.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.upload()
+        b.solve(arg_mixed)
+        b.download()
+        stream.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    st_e2e = b.all_stats()
+    e2e_ok = int(np.sum(st_e2e["status"] == 0))
+    e2e_val = a.batch / (statistics.mean(e2e_ms) * 1e-3)
+
+    # ---------------- batched FP64 and plain per-QP FP64 GPU baselines ----------------
+    for _ in range(2):
+        b.solve(arg_fp64)
+    barrier()
+    f64_ms = []
+    for _ in range(3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.solve(arg_fp64)
+        e1.record(stream)
+        e1.synchronize()
+        f64_ms.append(e0.elapsed_time(e1))
+    b.download()
+    torch.cuda.synchronize()
+    st64 = b.all_stats()
+    batched_fp64 = a.batch / (statistics.mean(f64_ms) * 1e-3)
+    plain_ms = []
+    plain_ok = 0
+    singles = [QpBatch([q], device=dev) for q in qps[:a.plain_sample]]
+    for sb in singles:
+        sb.upload()
+        sb.solve(arg_fp64)
+    torch.cuda.synchronize()
+    for sb in singles:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sb.solve(arg_fp64)
+        e1.record(stream)
+        e1.synchronize()
+        plain_ms.append(e0.elapsed_time(e1))
+        sb.download()
+        torch.cuda.synchronize()
+        plain_ok += int(sb.all_stats()["status"][0] == 0)
+    plain = {"value": 1e3 / statistics.mean(plain_ms), "unit": UNIT,
+             "p50_ms": float(np.percentile(plain_ms, 50)), "p99_ms": float(np.percentile(plain_ms, 99)),
+             "sample": f"{a.plain_sample} QPs, one launch each, FP64 Riccati", "converged": plain_ok}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": mean_ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch_per_gpu": a.batch, "horizon": HORIZON, "nx": 16, "nu": 7,
+                       "precision": "mixed (FP32 Riccati, FP64 residual/IR/step)", "kkt_tol": 1e-8,
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "p50_ms": p50, "p99_ms": p99,
+            "converged": conv, "fp64_fallback_qps": fallback,
+            "iters_mean": float(np.mean(st["iters"])), "ir_mean": float(np.mean(st["ir_total"])),
+            "gpu_launches": launches,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_eff / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / peak_eff if peak_eff == peak_eff else None, "traffic": None,
+                         "kernel": "ipm_kernel", "flops_f32": f32, "flops_f64": f64,
+                         "peak_note": "FP32 152 SMs x 128 lanes x 2 x 2.07 GHz = 80.5 TF; FP64 nominal 1.25 TF; "
+                                      "peak = flop-mix-weighted"},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(b.sizes.in_bytes),
+                    "d2h_bytes_per_step": int(b.sizes.sol_bytes), "converged": e2e_ok},
+            "batched_fp64_gpu": {"value": batched_fp64, "unit": UNIT, "ms": statistics.mean(f64_ms),
+                                 "converged": int(np.sum(st64["status"] == 0)),
+                                 "iters_mean": float(np.mean(st64["iters"]))},
+            "plain_fp64_gpu": plain,
+            "clocks": ck,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

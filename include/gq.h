@@ -1,0 +1,233 @@
+/*
+ * gq.h -- C ABI of the batched OCP-QP interior-point solver for GB300 (sm_103a).
+ *
+ * The library solves batches of optimal-control QPs (the OCP QP of Sec. 2.2 of
+ * the HPIPM paper, arXiv 2003.02547) with the primal-dual Mehrotra
+ * predictor-corrector interior-point method of Sec. 3.1-3.4 and 4.2.  The
+ * Newton system eq. (delta) is reduced to eq. (kkt) by eliminating dt and
+ * dlambda (Sec. 3.3) and factorised by the square-root backward Riccati
+ * recursion (Sec. 3.3, variant (b)); the whole IPM loop of every QP runs
+ * inside CUDA kernels, one thread block per QP.
+ *
+ * Problem statement (Sec. 2.2).  For stages n = 0..N, y_n = [u_n; x_n]:
+ *   min  sum_n 1/2 [u;x;1]' [[R, S, r], [S', Q, q], [r', q', 0]] [u;x;1]
+ *   s.t. x_{n+1} = A_n x_n + B_n u_n + b_n                 n = 0..N-1
+ *        lbu_n <= u_n[idxbu_n] <= ubu_n,  lbx_n <= x_n[idxbx_n] <= ubx_n
+ *        lg_n  <= D_n u_n + C_n x_n <= ug_n                 n = 0..N
+ * S_n has shape nu_n x nx_n.  Sizes may vary per stage and per QP.  A bound
+ * of -INFINITY (lower) or +INFINITY (upper) masks that single side (Sec. 2.1).
+ * An initial-state constraint is expressed either by eliminating x_0
+ * (nx_0 = 0, x0 folded into b_0, r_0 and the stage-0 general bounds) or, as
+ * in the paper, by a box on x_0 with equal bounds.
+ *
+ * Sign conventions of the outputs (Lagrangian of Sec. 3.1):
+ *   equality rows -B_n u_n - A_n x_n + x_{n+1} = b_n with multiplier pi_{n+1}
+ *   (pi_{n+1} is the cost-to-go gradient at x_{n+1});
+ *   each constraint lo <= c(y) <= hi gives the sides c(y) - lo >= 0 and
+ *   hi - c(y) >= 0; per stage the constraint list is [box u (idxbu order);
+ *   box x (idxbx order); general rows], nc_n = nbu_n + nbx_n + ng_n, and
+ *   lambda/t hold the nc_n lower sides followed by the nc_n upper sides.
+ *   Masked sides report lambda = 0, t = 1.
+ *
+ * Memory (Sec. 1: no internal allocation, externally provided chunks).
+ *   The library never allocates.  The caller provides
+ *     - the host memory of the batch handle            (gq_batch_memsize)
+ *     - a host "in" staging buffer and a device "in" buffer of equal size
+ *       holding descriptors, indices and FP64 problem data (sizes.in_bytes)
+ *     - a host and a device "sol" buffer of equal size holding per-QP
+ *       statistics and the iterates y, pi, lambda, t  (sizes.sol_bytes)
+ *     - a device workspace                             (sizes.ws_bytes)
+ *   Device buffers must be 256-byte aligned (cudaMalloc / PyTorch storage).
+ *   Host buffers should be pinned for asynchronous copies.
+ *
+ * Errors.  Every call returns 0 (GQ_OK) or a negative GQ_ERR_* code and never
+ * aborts, throws or traps; gq_last_error() gives a per-thread message.  Solve
+ * results carry a per-QP status (GQ_STATUS_*); a failing QP never affects its
+ * batch neighbours.
+ */
+#ifndef GQ_H
+#define GQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GQ_API __attribute__((visibility("default")))
+#else
+#define GQ_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define GQ_OK 0
+#define GQ_ERR_ARG -1     /* null pointer, index out of range, bad enum        */
+#define GQ_ERR_DIMS -2    /* inconsistent or unsupported dimensions            */
+#define GQ_ERR_SIZE -3    /* caller buffer smaller than required               */
+#define GQ_ERR_CUDA -4    /* a CUDA runtime call failed                        */
+#define GQ_ERR_DATA -5    /* NaN in data, lo > hi, non-symmetric Q/R, ...      */
+#define GQ_ERR_STATE -6   /* call made before the buffers it needs are attached */
+
+/* ---- per-QP solve status ---- */
+#define GQ_STATUS_CONVERGED 0
+#define GQ_STATUS_MAX_ITER 1
+#define GQ_STATUS_MIN_STEP 2
+#define GQ_STATUS_NAN 3      /* non-finite residual or non-positive pivot     */
+#define GQ_STATUS_TIMEOUT 4  /* arg.timeout_ns elapsed on the device          */
+/* flag bits in gq_stats.flags */
+#define GQ_FLAG_FP64_FALLBACK 1  /* mixed path switched this QP to FP64 factors */
+
+/* ---- solver arguments (Sec. 4.2) ---- */
+#define GQ_MODE_SPEED 0     /* delta formulation, residual-based exit (Sec. 4.2) */
+#define GQ_MODE_BALANCE 1   /* speed + iterative refinement of every direction   */
+#define GQ_PREC_FP64 0      /* Riccati factor/solve in FP64                       */
+#define GQ_PREC_MIXED 1     /* Riccati factor/solve in FP32, residuals, IR,
+                               step length and duality measure in FP64          */
+
+typedef struct gq_ipm_arg {
+    int32_t mode;          /* GQ_MODE_*                                            */
+    int32_t precision;     /* GQ_PREC_*                                            */
+    int32_t iter_max;      /* maximum IPM iterations                               */
+    int32_t warm_start;    /* 0 cold, 1 primal (y, pi), 2 primal + dual (Sec. 4.2) */
+    int32_t ir_steps;      /* max iterative-refinement steps per direction (3.4)   */
+    int32_t cond_corr;     /* 1: conditional Mehrotra corrector (Sec. 4.2)         */
+    int32_t fp64_fallback; /* mixed path: 1 = refactor in FP64 when IR stagnates   */
+    int32_t reserved0;
+    double tol_stat;       /* exit: ||r_g||inf <= tol_stat                          */
+    double tol_eq;         /*       ||r_b||inf <= tol_eq                            */
+    double tol_ineq;       /*       ||r_d||inf <= tol_ineq                          */
+    double tol_comp;       /*       mu = lambda't / n_c <= tol_comp                 */
+    double alpha_min;      /* exit when the step length drops below this           */
+    double lam_min;        /* lower clamp of lambda after each step (Sec. 4.2)     */
+    double t_min;          /* lower clamp of t after each step                     */
+    double tau_b;          /* fraction to the boundary, alpha = min(1, tau_b a_max) */
+    double corr_k;         /* keep corrector if mu_corr <= corr_k * mu_aff          */
+    double reg_prim;       /* primal regularisation added to the factored Hessian
+                              only (Sec. 4.2); offset by IR                         */
+    double ir_tol;         /* IR stops when ||res||inf <= ir_tol ||rhs||inf          */
+    double warm_min;       /* warm start 2: lambda, t clamped below by this         */
+    int64_t timeout_ns;    /* per-QP device wall-clock limit, 0 = none             */
+} gq_ipm_arg;
+
+/* Defaults for a mode and precision: iter_max 100, tolerances 1e-8,
+ * alpha_min 1e-12, lam_min = t_min = 1e-16 (FP64) or 1e-12 (mixed),
+ * tau_b 0.995, corr_k 2, reg_prim 0 (FP64) or 1e-9 (mixed), ir_steps 0
+ * (FP64 speed) or 3 (mixed or balance), ir_tol 1e-12, warm_min 1e-2.
+ * Returns GQ_ERR_ARG on a null pointer or unknown mode/precision. */
+GQ_API int gq_ipm_arg_default(gq_ipm_arg* arg, int mode, int precision);
+
+/* ---- per-QP results ---- */
+typedef struct gq_stats {
+    int32_t status;        /* GQ_STATUS_*                                          */
+    int32_t iters;         /* IPM iterations taken                                 */
+    int32_t flags;         /* GQ_FLAG_* bits                                       */
+    int32_t ir_total;      /* iterative-refinement solves performed                */
+    int32_t n_fact;        /* Riccati factorisations (all precisions)              */
+    int32_t n_fact64;      /*   of which in FP64                                   */
+    int32_t n_solve;       /* Riccati solves (all right-hand sides)                */
+    int32_t n_res;         /* residual evaluations (IPM and refinement)            */
+    double res[4];         /* ||r_g||inf, ||r_b||inf, ||r_d||inf, mu at exit        */
+} gq_stats;
+
+/* ---- batch layout ---- */
+typedef struct gq_batch gq_batch;
+
+typedef struct gq_sizes {
+    size_t in_bytes;       /* host staging == device "in" buffer                   */
+    size_t sol_bytes;      /* host == device solution buffer                       */
+    size_t ws_bytes;       /* device workspace                                     */
+    int64_t n_stages;      /* total stages over the batch                          */
+    int64_t n_slots;       /* distinct stage data blocks                           */
+    int64_t nv_total;      /* sum of nu_n + nx_n over the batch                    */
+    int64_t neq_total;     /* sum of nx_{n+1}                                      */
+    int64_t nside_total;   /* sum of 2 (nbu_n + nbx_n + ng_n)                      */
+    int32_t nv_max;        /* largest stage nu_n + nx_n                            */
+    int32_t nx_max;        /* largest stage nx_n                                   */
+} gq_sizes;
+
+/* dims: for QP q in order, N_q followed by (N_q + 1) groups of five ints
+ * (nx_n, nu_n, nbx_n, nbu_n, ng_n), n = 0..N_q.  Requires nx_n >= 0,
+ * nu_n >= 0, 0 <= nbu_n <= nu_n, 0 <= nbx_n <= nx_n, ng_n >= 0, N_q >= 0.
+ * stage_slot (may be NULL): one int per stage in the same order; stages with
+ * equal non-negative slot ids share one problem-data block (they must have
+ * identical sizes, including nx_{n+1}); NULL or -1 gives a private block.
+ * Returns the host bytes the batch handle needs, or 0 on invalid input. */
+GQ_API size_t gq_batch_memsize(int nqp, const int* dims, size_t dims_len, const int* stage_slot);
+
+/* Lays the batch out in the caller's host memory `mem` (>= memsize bytes,
+ * 16-byte aligned) and returns the handle in *out.  The handle stays valid
+ * while `mem` does; there is no destroy call. */
+GQ_API int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_slot,
+                    void* mem, size_t mem_bytes, gq_batch** out);
+
+GQ_API int gq_batch_sizes(const gq_batch* b, gq_sizes* out);
+
+/* Attaches the caller-owned buffers.  host_in/host_sol may be NULL when
+ * setters/getters are not used; dev_* must be non-NULL, 256-byte aligned.
+ * Writes the layout descriptors into host_in (if given). */
+GQ_API int gq_batch_attach(gq_batch* b, void* host_in, void* host_sol,
+                    void* dev_in, void* dev_sol, void* dev_ws);
+
+/* ---- data setters: write FP64 data of stage n of QP qp into host_in ----
+ * Matrices are column-major with leading dimension >= their row count.
+ * A: nx_{n+1} x nx_n, B: nx_{n+1} x nu_n, b: nx_{n+1} (Sec. 2.2 dynamics). */
+GQ_API int gq_set_dynamics(gq_batch* b, int qp, int n, const double* A, int lda,
+                    const double* B, int ldb, const double* bvec);
+/* Q: nx_n x nx_n, S: nu_n x nx_n, R: nu_n x nu_n (Q, R symmetric), q, r. */
+GQ_API int gq_set_cost(gq_batch* b, int qp, int n, const double* Q, int ldq, const double* S, int lds,
+                const double* R, int ldr, const double* q, const double* r);
+/* idxbu: nbu_n distinct indices into u_n; idxbx: nbx_n distinct into x_n;
+ * bounds with lo <= hi, +-INFINITY masks a side. */
+GQ_API int gq_set_box(gq_batch* b, int qp, int n, const int* idxbu, const double* lbu, const double* ubu,
+               const int* idxbx, const double* lbx, const double* ubx);
+/* C: ng_n x nx_n, D: ng_n x nu_n, lg, ug: ng_n. */
+GQ_API int gq_set_general(gq_batch* b, int qp, int n, const double* C, int ldc, const double* D, int ldd,
+                   const double* lg, const double* ug);
+
+/* Writes an initial guess for QP qp into host_sol (y: sum nv entries in stage
+ * order [u_0; x_0; u_1; ...], pi: sum nx_{n+1}, lam/t: sum 2 nc_n; any may be
+ * NULL to leave that part unchanged).  Used with arg.warm_start after
+ * gq_upload_sol. */
+GQ_API int gq_set_guess(gq_batch* b, int qp, const double* y, const double* pi,
+                 const double* lam, const double* t);
+
+/* ---- transfers (asynchronous on `stream`, a cudaStream_t; NULL = legacy) ---- */
+GQ_API int gq_upload(gq_batch* b, void* stream);       /* host_in  -> dev_in  */
+GQ_API int gq_upload_sol(gq_batch* b, void* stream);   /* host_sol -> dev_sol */
+GQ_API int gq_download(gq_batch* b, void* stream);     /* dev_sol  -> host_sol */
+
+/* ---- solve (Sec. 4.2): enqueue the IPM for every QP of the batch ----
+ * Asynchronous: one kernel launch on `stream`; results appear in dev_sol.
+ * Errors in the arguments are reported before anything is enqueued. */
+GQ_API int gq_solve(gq_batch* b, const gq_ipm_arg* arg, void* stream);
+
+/* Row-level entry points, used to check the solver step by step.
+ * gq_residuals: residual function of eq. (delta) at the iterate in dev_sol;
+ *   writes per-QP norms into the stats res[] fields (status left as is).
+ * gq_newton_step: one Newton direction of eq. (delta) at the iterate in dev_sol
+ *   with r_m = lambda t - sigma_mu, through the Riccati factorisation of
+ *   eq. (kkt) in the precision of arg; writes (dy, dpi, dlambda, dt) into
+ *   dev_dir, a device buffer laid out like the iterate part of the sol buffer
+ *   (sizes.sol_bytes bytes; its stats part is left untouched). */
+GQ_API int gq_residuals(gq_batch* b, void* stream);
+GQ_API int gq_newton_step(gq_batch* b, const gq_ipm_arg* arg, double sigma_mu, void* dev_dir, void* stream);
+
+/* ---- getters (read host_sol after gq_download + stream sync) ---- */
+/* u: nu_n, x: nx_n, pi: nx_{n+1} (n < N; multiplier of dynamics block n),
+ * lam, t: 2 nc_n.  Any pointer may be NULL. */
+GQ_API int gq_get_stage_sol(const gq_batch* b, int qp, int n, double* u, double* x, double* pi,
+                     double* lam, double* t);
+GQ_API int gq_get_stats(const gq_batch* b, int qp, gq_stats* out);
+/* Offsets (in doubles) of QP qp's vectors inside the sol buffer:
+ * off[0] y, off[1] pi, off[2] lam, off[3] t, and their lengths off[4..7]. */
+GQ_API int gq_get_sol_offsets(const gq_batch* b, int qp, int64_t off[8]);
+
+/* Per-thread description of the last error, never NULL. */
+GQ_API const char* gq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GQ_H */

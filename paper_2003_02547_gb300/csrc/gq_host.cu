@@ -1,0 +1,715 @@
+// Host side of the gq C ABI: batch layout planning, validated setters and
+// getters, transfers and the solve entry point.  Nothing here allocates: all
+// memory comes from the caller (Sec. 1 of the HPIPM paper: the solver works on
+// externally provided chunks of memory).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "gq_internal.h"
+#include "gq_launch.h"
+
+using namespace gq;
+
+namespace {
+
+thread_local char g_err[512] = "no error";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(GQ_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr uint32_t kMagic = 0x67716231u;  // "gqb1"
+
+int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+struct SlotEntry {
+  int64_t key;    // slot id, -1 = empty
+  int64_t block;  // data offset (doubles)
+  int32_t stage;  // first stage using this slot
+  int32_t idx;    // box-index offset (ints), shared like the data block
+};
+
+}  // namespace
+
+struct gq_batch {
+  uint32_t magic;
+  int32_t nqp;
+  int64_t n_stages, n_slots, hash_cap;
+  Layout L;
+  gq_sizes sizes;
+  int32_t ngmax;
+  Shape shape;
+  QpDesc* qp;
+  StageDesc* st;
+  int32_t* order;
+  SlotEntry* hash;
+  void *host_in, *host_sol, *dev_in, *dev_sol, *dev_ws;
+};
+
+namespace {
+
+struct Counts {
+  int64_t n_stages = 0;
+  bool ok = false;
+};
+
+// Parses dims and checks their consistency; returns the stage count.
+Counts count_stages(int nqp, const int* dims, size_t dims_len) {
+  Counts c;
+  if (nqp <= 0 || dims == nullptr) {
+    fail(GQ_ERR_ARG, "nqp must be positive and dims non-NULL");
+    return c;
+  }
+  size_t pos = 0;
+  for (int q = 0; q < nqp; ++q) {
+    if (pos >= dims_len) {
+      fail(GQ_ERR_DIMS, "dims too short at QP %d", q);
+      return c;
+    }
+    const int N = dims[pos++];
+    if (N < 0 || N > (1 << 20)) {
+      fail(GQ_ERR_DIMS, "QP %d: horizon N=%d out of range", q, N);
+      return c;
+    }
+    if (pos + 5 * (size_t)(N + 1) > dims_len) {
+      fail(GQ_ERR_DIMS, "dims too short for QP %d (N=%d)", q, N);
+      return c;
+    }
+    for (int n = 0; n <= N; ++n) {
+      const int* d = dims + pos + 5 * n;
+      const int nx = d[0], nu = d[1], nbx = d[2], nbu = d[3], ng = d[4];
+      if (nx < 0 || nu < 0 || nbx < 0 || nbu < 0 || ng < 0 || nbx > nx || nbu > nu ||
+          nx > 4096 || nu > 4096 || ng > 65536) {
+        fail(GQ_ERR_DIMS, "QP %d stage %d: invalid sizes nx=%d nu=%d nbx=%d nbu=%d ng=%d", q, n,
+             nx, nu, nbx, nbu, ng);
+        return c;
+      }
+      if (nx + nu == 0) {
+        fail(GQ_ERR_DIMS, "QP %d stage %d: stage without variables", q, n);
+        return c;
+      }
+    }
+    pos += 5 * (size_t)(N + 1);
+    c.n_stages += N + 1;
+  }
+  if (pos != dims_len) {
+    fail(GQ_ERR_DIMS, "dims has %zu trailing entries", dims_len - pos);
+    return c;
+  }
+  c.ok = true;
+  return c;
+}
+
+int64_t hash_capacity(int64_t n) {
+  int64_t cap = 16;
+  while (cap < 2 * n) cap <<= 1;
+  return cap;
+}
+
+size_t handle_bytes(int nqp, int64_t n_stages, int64_t cap) {
+  int64_t b = align_up(sizeof(gq_batch), 64);
+  b += align_up((int64_t)nqp * sizeof(QpDesc), 64);
+  b += align_up(n_stages * sizeof(StageDesc), 64);
+  b += align_up((int64_t)nqp * sizeof(int32_t), 64);
+  b += align_up(cap * sizeof(SlotEntry), 64);
+  return (size_t)b;
+}
+
+inline double* host_data(gq_batch* b) {
+  return reinterpret_cast<double*>(static_cast<char*>(b->host_in) + b->L.data);
+}
+inline int32_t* host_idx(gq_batch* b) {
+  return reinterpret_cast<int32_t*>(static_cast<char*>(b->host_in) + b->L.idx);
+}
+
+int check_batch(const gq_batch* b) {
+  if (b == nullptr || b->magic != kMagic) return fail(GQ_ERR_ARG, "invalid batch handle");
+  return GQ_OK;
+}
+
+int stage_of(gq_batch* b, int qp, int n, StageDesc** out) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (qp < 0 || qp >= b->nqp) return fail(GQ_ERR_ARG, "qp %d out of range [0,%d)", qp, b->nqp);
+  const QpDesc& d = b->qp[qp];
+  if (n < 0 || n > d.N) return fail(GQ_ERR_ARG, "stage %d out of range [0,%d] for QP %d", n, d.N, qp);
+  if (b->host_in == nullptr) return fail(GQ_ERR_STATE, "host_in buffer not attached");
+  *out = &b->st[d.stage0 + n];
+  return GQ_OK;
+}
+
+bool finite_all(const double* v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gq_last_error(void) { return g_err; }
+
+int gq_ipm_arg_default(gq_ipm_arg* arg, int mode, int precision) {
+  if (arg == nullptr) return fail(GQ_ERR_ARG, "arg is NULL");
+  if (mode != GQ_MODE_SPEED && mode != GQ_MODE_BALANCE) return fail(GQ_ERR_ARG, "unknown mode %d", mode);
+  if (precision != GQ_PREC_FP64 && precision != GQ_PREC_MIXED)
+    return fail(GQ_ERR_ARG, "unknown precision %d", precision);
+  std::memset(arg, 0, sizeof(*arg));
+  arg->mode = mode;
+  arg->precision = precision;
+  arg->iter_max = 100;
+  arg->warm_start = 0;
+  arg->cond_corr = 1;
+  arg->fp64_fallback = 1;
+  arg->tol_stat = arg->tol_eq = arg->tol_ineq = arg->tol_comp = 1e-8;
+  arg->alpha_min = 1e-12;
+  const bool mixed = precision == GQ_PREC_MIXED;
+  arg->lam_min = arg->t_min = mixed ? 1e-12 : 1e-16;
+  arg->tau_b = 0.995;
+  arg->corr_k = 2.0;
+  arg->reg_prim = mixed ? 1e-9 : 0.0;
+  arg->ir_steps = (mixed || mode == GQ_MODE_BALANCE) ? 3 : 0;
+  arg->ir_tol = 1e-12;
+  arg->warm_min = 1e-2;
+  arg->timeout_ns = 0;
+  return GQ_OK;
+}
+
+size_t gq_batch_memsize(int nqp, const int* dims, size_t dims_len, const int* stage_slot) {
+  (void)stage_slot;
+  Counts c = count_stages(nqp, dims, dims_len);
+  if (!c.ok) return 0;
+  return handle_bytes(nqp, c.n_stages, hash_capacity(c.n_stages));
+}
+
+int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_slot, void* mem,
+                    size_t mem_bytes, gq_batch** out) {
+  if (out == nullptr || mem == nullptr) return fail(GQ_ERR_ARG, "mem and out must be non-NULL");
+  *out = nullptr;
+  if (reinterpret_cast<uintptr_t>(mem) % 16) return fail(GQ_ERR_ARG, "mem must be 16-byte aligned");
+  Counts c = count_stages(nqp, dims, dims_len);
+  if (!c.ok) return GQ_ERR_DIMS;
+  const int64_t cap = hash_capacity(c.n_stages);
+  const size_t need = handle_bytes(nqp, c.n_stages, cap);
+  if (mem_bytes < need) return fail(GQ_ERR_SIZE, "handle memory %zu < %zu bytes", mem_bytes, need);
+
+  char* p = static_cast<char*>(mem);
+  gq_batch* b = reinterpret_cast<gq_batch*>(p);
+  std::memset(b, 0, sizeof(gq_batch));
+  p += align_up(sizeof(gq_batch), 64);
+  b->qp = reinterpret_cast<QpDesc*>(p);
+  p += align_up((int64_t)nqp * sizeof(QpDesc), 64);
+  b->st = reinterpret_cast<StageDesc*>(p);
+  p += align_up(c.n_stages * sizeof(StageDesc), 64);
+  b->order = reinterpret_cast<int32_t*>(p);
+  p += align_up((int64_t)nqp * sizeof(int32_t), 64);
+  b->hash = reinterpret_cast<SlotEntry*>(p);
+  b->hash_cap = cap;
+  for (int64_t i = 0; i < cap; ++i) b->hash[i].key = -1;
+  b->nqp = nqp;
+  b->n_stages = c.n_stages;
+
+  // walk the dims: stage descriptors, vector offsets, data blocks
+  int64_t var = 0, eq = 0, side = 0, idx = 0, data = 0, fac = 0, slots = 0;
+  int nvmax = 0, nxmax = 0, ngmax = 0, nstmax = 0, nemax = 0, nsidemax = 0;
+  size_t pos = 0;
+  int64_t si = 0;
+  for (int q = 0; q < nqp; ++q) {
+    const int N = dims[pos++];
+    QpDesc& d = b->qp[q];
+    std::memset(&d, 0, sizeof(d));
+    d.N = N;
+    d.stage0 = (int32_t)si;
+    d.var0 = (int32_t)var;
+    d.eq0 = (int32_t)eq;
+    d.side0 = (int32_t)side;
+    nstmax = std::max(nstmax, N + 1);
+    double cost = 0.0;
+    for (int n = 0; n <= N; ++n, ++si) {
+      const int* dn = dims + pos + 5 * n;
+      StageDesc& s = b->st[si];
+      s.nx = dn[0];
+      s.nu = dn[1];
+      s.nbx = dn[2];
+      s.nbu = dn[3];
+      s.ng = dn[4];
+      s.nx1 = (n < N) ? dims[pos + 5 * (n + 1)] : 0;
+      const int nv = s.nx + s.nu, nb = s.nbx + s.nbu, nc = nb + s.ng;
+      s.var = (int32_t)var;
+      s.eq = (int32_t)eq;
+      s.side = (int32_t)side;
+      s.fac = fac;
+      var += nv;
+      eq += s.nx1;
+      side += 2 * nc;
+      fac += (int64_t)nv * nv;
+      nvmax = std::max(nvmax, nv);
+      nxmax = std::max(nxmax, s.nx);
+      nemax = std::max(nemax, n == 0 ? nv : s.nu);
+      ngmax = std::max(ngmax, s.ng);
+      d.nvmax = std::max(d.nvmax, nv);
+      d.nxmax = std::max(d.nxmax, s.nx);
+      cost += (double)s.nx1 * s.nx1 * nv + (double)s.nx1 * nv * nv + (double)nv * nv * nv / 3.0 +
+              (double)s.ng * nv * nv;
+      const StageData lay = stage_data_layout(s.nx, s.nu, s.nx1, nb, s.ng);
+      const int slot = stage_slot ? stage_slot[si] : -1;
+      if (slot < 0) {
+        s.data = data;
+        s.idx = (int32_t)idx;
+        data += lay.size;
+        idx += nb;
+        ++slots;
+      } else {
+        int64_t h = ((uint64_t)slot * 0x9E3779B97F4A7C15ull) & (cap - 1);
+        while (b->hash[h].key != -1 && b->hash[h].key != slot) h = (h + 1) & (cap - 1);
+        if (b->hash[h].key == -1) {
+          b->hash[h].key = slot;
+          b->hash[h].block = data;
+          b->hash[h].stage = (int32_t)si;
+          b->hash[h].idx = (int32_t)idx;
+          s.data = data;
+          s.idx = (int32_t)idx;
+          data += lay.size;
+          idx += nb;
+          ++slots;
+        } else {
+          const StageDesc& f = b->st[b->hash[h].stage];
+          if (f.nx != s.nx || f.nu != s.nu || f.nx1 != s.nx1 || f.nbx != s.nbx || f.nbu != s.nbu ||
+              f.ng != s.ng)
+            return fail(GQ_ERR_DIMS, "QP %d stage %d shares slot %d with a stage of other sizes", q, n,
+                        slot);
+          s.data = b->hash[h].block;
+          s.idx = b->hash[h].idx;
+        }
+      }
+    }
+    pos += 5 * (size_t)(N + 1);
+    d.nvt = (int32_t)(var - d.var0);
+    d.neqt = (int32_t)(eq - d.eq0);
+    d.nsidet = (int32_t)(side - d.side0);
+    d.cost = cost;
+    nsidemax = std::max(nsidemax, d.nsidet);
+  }
+  if (var >= INT32_MAX || eq >= INT32_MAX || side >= INT32_MAX || idx >= INT32_MAX)
+    return fail(GQ_ERR_DIMS, "batch too large for 32-bit vector offsets");
+
+  // longest-processing-time order: most expensive QPs launch first
+  for (int q = 0; q < nqp; ++q) b->order[q] = q;
+  QpDesc* qd = b->qp;
+  std::stable_sort(b->order, b->order + nqp,
+                   [qd](int32_t a, int32_t c2) { return qd[a].cost > qd[c2].cost; });
+
+  Layout& L = b->L;
+  int64_t o = 0;
+  L.qpdesc = o;
+  o = align_up(o + (int64_t)nqp * sizeof(QpDesc), 256);
+  L.stagedesc = o;
+  o = align_up(o + c.n_stages * sizeof(StageDesc), 256);
+  L.order = o;
+  o = align_up(o + (int64_t)nqp * 4, 256);
+  L.idx = o;
+  o = align_up(o + idx * 4, 256);
+  L.data = o;
+  o = align_up(o + data * 8, 256);
+  L.in_bytes = o;
+
+  o = 0;
+  L.stats = o;
+  o = align_up(o + (int64_t)nqp * sizeof(gq_stats), 256);
+  L.y = o;
+  o = align_up(o + var * 8, 256);
+  L.pi = o;
+  o = align_up(o + eq * 8, 256);
+  L.lam = o;
+  o = align_up(o + side * 8, 256);
+  L.t = o;
+  o = align_up(o + side * 8, 256);
+  L.sol_bytes = o;
+
+  o = 0;
+  int64_t* vecs[] = {&L.rg, &L.rb, &L.rd, &L.rm, &L.gt, &L.dy, &L.dpi, &L.dlam, &L.dt, &L.lp,
+                     &L.rg2, &L.rb2, &L.dy2, &L.dpi2};
+  const int64_t lens[] = {var, eq, side, side, var, var, eq, side, side, var, var, eq, var, eq};
+  for (int i = 0; i < 14; ++i) {
+    *vecs[i] = o;
+    o = align_up(o + lens[i] * 8, 256);
+  }
+  L.fac = o;
+  o = align_up(o + fac * 8, 256);
+  L.ws_bytes = o;
+
+  gq_sizes& z = b->sizes;
+  z.in_bytes = (size_t)L.in_bytes;
+  z.sol_bytes = (size_t)L.sol_bytes;
+  z.ws_bytes = (size_t)L.ws_bytes;
+  z.n_stages = c.n_stages;
+  z.n_slots = slots;
+  z.nv_total = var;
+  z.neq_total = eq;
+  z.nside_total = side;
+  z.nv_max = nvmax;
+  z.nx_max = nxmax;
+  b->ngmax = ngmax;
+  b->shape.nst_max = nstmax;
+  b->shape.ne_max = nemax;
+  b->shape.nside_max = nsidemax;
+  b->n_slots = slots;
+  b->magic = kMagic;
+  *out = b;
+  return GQ_OK;
+}
+
+int gq_batch_sizes(const gq_batch* b, gq_sizes* out) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (out == nullptr) return fail(GQ_ERR_ARG, "out is NULL");
+  *out = b->sizes;
+  return GQ_OK;
+}
+
+int gq_batch_attach(gq_batch* b, void* host_in, void* host_sol, void* dev_in, void* dev_sol,
+                    void* dev_ws) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (dev_in == nullptr || dev_sol == nullptr || dev_ws == nullptr)
+    return fail(GQ_ERR_ARG, "device buffers must be non-NULL");
+  for (void* p : {dev_in, dev_sol, dev_ws})
+    if (reinterpret_cast<uintptr_t>(p) % 256) return fail(GQ_ERR_ARG, "device buffers must be 256-byte aligned");
+  for (void* p : {host_in, host_sol})
+    if (p && reinterpret_cast<uintptr_t>(p) % 16) return fail(GQ_ERR_ARG, "host buffers must be 16-byte aligned");
+  b->host_in = host_in;
+  b->host_sol = host_sol;
+  b->dev_in = dev_in;
+  b->dev_sol = dev_sol;
+  b->dev_ws = dev_ws;
+  if (host_in) {
+    char* h = static_cast<char*>(host_in);
+    std::memset(h + b->L.idx, 0, (size_t)(b->L.in_bytes - b->L.idx));
+    std::memcpy(h + b->L.qpdesc, b->qp, (size_t)b->nqp * sizeof(QpDesc));
+    std::memcpy(h + b->L.stagedesc, b->st, (size_t)b->n_stages * sizeof(StageDesc));
+    std::memcpy(h + b->L.order, b->order, (size_t)b->nqp * sizeof(int32_t));
+  }
+  return GQ_OK;
+}
+
+int gq_set_dynamics(gq_batch* b, int qp, int n, const double* A, int lda, const double* B, int ldb,
+                    const double* bvec) {
+  StageDesc* s;
+  int rc = stage_of(b, qp, n, &s);
+  if (rc) return rc;
+  if (n == b->qp[qp].N) return fail(GQ_ERR_ARG, "stage %d is terminal: no dynamics", n);
+  const int nx = s->nx, nu = s->nu, nx1 = s->nx1;
+  if ((nx && A == nullptr) || (nu && B == nullptr) || bvec == nullptr)
+    return fail(GQ_ERR_ARG, "dynamics pointers must be non-NULL");
+  if ((nx && lda < nx1) || (nu && ldb < nx1)) return fail(GQ_ERR_ARG, "leading dimension too small");
+  const StageData lay = stage_data_layout(nx, nu, nx1, s->nbu + s->nbx, s->ng);
+  double* D = host_data(b) + s->data;
+  for (int i = 0; i < nu; ++i)
+    for (int k = 0; k < nx1; ++k) D[lay.BAt + (int64_t)i * nx1 + k] = B[k + (int64_t)i * ldb];
+  for (int i = 0; i < nx; ++i)
+    for (int k = 0; k < nx1; ++k) D[lay.BAt + (int64_t)(nu + i) * nx1 + k] = A[k + (int64_t)i * lda];
+  for (int k = 0; k < nx1; ++k) D[lay.b + k] = bvec[k];
+  if (!finite_all(D + lay.BAt, (nu + nx) * nx1 + nx1)) return fail(GQ_ERR_DATA, "non-finite dynamics data");
+  return GQ_OK;
+}
+
+int gq_set_cost(gq_batch* b, int qp, int n, const double* Q, int ldq, const double* S, int lds,
+                const double* R, int ldr, const double* q, const double* r) {
+  StageDesc* s;
+  int rc = stage_of(b, qp, n, &s);
+  if (rc) return rc;
+  const int nx = s->nx, nu = s->nu, nv = nx + nu;
+  if ((nx && (Q == nullptr || q == nullptr)) || (nu && (R == nullptr || r == nullptr)) ||
+      (nx && nu && S == nullptr))
+    return fail(GQ_ERR_ARG, "cost pointers must be non-NULL");
+  if ((nx && ldq < nx) || (nu && ldr < nu) || (nx && nu && lds < nu))
+    return fail(GQ_ERR_ARG, "leading dimension too small");
+  for (int i = 0; i < nx; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double a = Q[i + (int64_t)j * ldq], c = Q[j + (int64_t)i * ldq];
+      if (!(std::fabs(a - c) <= 1e-12 * (1.0 + std::fabs(a)))) return fail(GQ_ERR_DATA, "Q not symmetric");
+    }
+  for (int i = 0; i < nu; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double a = R[i + (int64_t)j * ldr], c = R[j + (int64_t)i * ldr];
+      if (!(std::fabs(a - c) <= 1e-12 * (1.0 + std::fabs(a)))) return fail(GQ_ERR_DATA, "R not symmetric");
+    }
+  const StageData lay = stage_data_layout(nx, nu, s->nx1, s->nbu + s->nbx, s->ng);
+  double* D = host_data(b) + s->data;
+  double* RSQ = D + lay.RSQ;
+  for (int i = 0; i < nu; ++i)
+    for (int j = 0; j < nu; ++j) RSQ[(int64_t)i * nv + j] = R[i + (int64_t)j * ldr];
+  for (int i = 0; i < nu; ++i)
+    for (int j = 0; j < nx; ++j) {
+      const double v = S[i + (int64_t)j * lds];
+      RSQ[(int64_t)i * nv + nu + j] = v;
+      RSQ[(int64_t)(nu + j) * nv + i] = v;
+    }
+  for (int i = 0; i < nx; ++i)
+    for (int j = 0; j < nx; ++j) RSQ[(int64_t)(nu + i) * nv + nu + j] = Q[i + (int64_t)j * ldq];
+  for (int i = 0; i < nu; ++i) D[lay.rq + i] = r[i];
+  for (int i = 0; i < nx; ++i) D[lay.rq + nu + i] = q[i];
+  if (!finite_all(RSQ, nv * nv + nv)) return fail(GQ_ERR_DATA, "non-finite cost data");
+  return GQ_OK;
+}
+
+int gq_set_box(gq_batch* b, int qp, int n, const int* idxbu, const double* lbu, const double* ubu,
+               const int* idxbx, const double* lbx, const double* ubx) {
+  StageDesc* s;
+  int rc = stage_of(b, qp, n, &s);
+  if (rc) return rc;
+  const int nbu = s->nbu, nbx = s->nbx, nb = nbu + nbx, nc = nb + s->ng;
+  if ((nbu && (idxbu == nullptr || lbu == nullptr || ubu == nullptr)) ||
+      (nbx && (idxbx == nullptr || lbx == nullptr || ubx == nullptr)))
+    return fail(GQ_ERR_ARG, "box pointers must be non-NULL");
+  const StageData lay = stage_data_layout(s->nx, s->nu, s->nx1, nb, s->ng);
+  double* D = host_data(b) + s->data;
+  int32_t* I = host_idx(b) + s->idx;
+  for (int k = 0; k < nbu; ++k) {
+    if (idxbu[k] < 0 || idxbu[k] >= s->nu) return fail(GQ_ERR_ARG, "idxbu[%d]=%d out of range", k, idxbu[k]);
+    for (int j = 0; j < k; ++j)
+      if (idxbu[j] == idxbu[k]) return fail(GQ_ERR_ARG, "idxbu has a repeated index %d", idxbu[k]);
+    I[k] = idxbu[k];
+    D[lay.lo + k] = lbu[k];
+    D[lay.hi + k] = ubu[k];
+  }
+  for (int k = 0; k < nbx; ++k) {
+    if (idxbx[k] < 0 || idxbx[k] >= s->nx) return fail(GQ_ERR_ARG, "idxbx[%d]=%d out of range", k, idxbx[k]);
+    for (int j = 0; j < k; ++j)
+      if (idxbx[j] == idxbx[k]) return fail(GQ_ERR_ARG, "idxbx has a repeated index %d", idxbx[k]);
+    I[nbu + k] = s->nu + idxbx[k];
+    D[lay.lo + nbu + k] = lbx[k];
+    D[lay.hi + nbu + k] = ubx[k];
+  }
+  for (int k = 0; k < nb; ++k) {
+    const double lo = D[lay.lo + k], hi = D[lay.hi + k];
+    if (std::isnan(lo) || std::isnan(hi) || lo > hi || lo == INFINITY || hi == -INFINITY)
+      return fail(GQ_ERR_DATA, "box bound %d invalid (lo=%g hi=%g)", k, lo, hi);
+  }
+  (void)nc;
+  return GQ_OK;
+}
+
+int gq_set_general(gq_batch* b, int qp, int n, const double* C, int ldc, const double* Dm, int ldd,
+                   const double* lg, const double* ug) {
+  StageDesc* s;
+  int rc = stage_of(b, qp, n, &s);
+  if (rc) return rc;
+  const int ng = s->ng, nx = s->nx, nu = s->nu, nv = nx + nu, nb = s->nbu + s->nbx;
+  if (ng == 0) return GQ_OK;
+  if ((nx && C == nullptr) || (nu && Dm == nullptr) || lg == nullptr || ug == nullptr)
+    return fail(GQ_ERR_ARG, "general-constraint pointers must be non-NULL");
+  if ((nx && ldc < ng) || (nu && ldd < ng)) return fail(GQ_ERR_ARG, "leading dimension too small");
+  const StageData lay = stage_data_layout(nx, nu, s->nx1, nb, ng);
+  double* D = host_data(b) + s->data;
+  for (int g = 0; g < ng; ++g) {
+    for (int i = 0; i < nu; ++i) D[lay.DC + (int64_t)g * nv + i] = Dm[g + (int64_t)i * ldd];
+    for (int i = 0; i < nx; ++i) D[lay.DC + (int64_t)g * nv + nu + i] = C[g + (int64_t)i * ldc];
+    const double lo = lg[g], hi = ug[g];
+    if (std::isnan(lo) || std::isnan(hi) || lo > hi || lo == INFINITY || hi == -INFINITY)
+      return fail(GQ_ERR_DATA, "general bound %d invalid (lo=%g hi=%g)", g, lo, hi);
+    D[lay.lo + nb + g] = lo;
+    D[lay.hi + nb + g] = hi;
+  }
+  if (!finite_all(D + lay.DC, ng * nv)) return fail(GQ_ERR_DATA, "non-finite general-constraint data");
+  return GQ_OK;
+}
+
+int gq_set_guess(gq_batch* b, int qp, const double* y, const double* pi, const double* lam,
+                 const double* t) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (qp < 0 || qp >= b->nqp) return fail(GQ_ERR_ARG, "qp out of range");
+  if (b->host_sol == nullptr) return fail(GQ_ERR_STATE, "host_sol not attached");
+  const QpDesc& d = b->qp[qp];
+  char* h = static_cast<char*>(b->host_sol);
+  if (y) std::memcpy(h + b->L.y + 8 * (int64_t)d.var0, y, 8 * (size_t)d.nvt);
+  if (pi) std::memcpy(h + b->L.pi + 8 * (int64_t)d.eq0, pi, 8 * (size_t)d.neqt);
+  if (lam) std::memcpy(h + b->L.lam + 8 * (int64_t)d.side0, lam, 8 * (size_t)d.nsidet);
+  if (t) std::memcpy(h + b->L.t + 8 * (int64_t)d.side0, t, 8 * (size_t)d.nsidet);
+  return GQ_OK;
+}
+
+static int copy(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, void* stream,
+                const char* what) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return GQ_OK;
+}
+
+int gq_upload(gq_batch* b, void* stream) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (!b->host_in || !b->dev_in) return fail(GQ_ERR_STATE, "buffers not attached");
+  return copy(b->dev_in, b->host_in, b->sizes.in_bytes, cudaMemcpyHostToDevice, stream, "upload");
+}
+
+int gq_upload_sol(gq_batch* b, void* stream) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (!b->host_sol || !b->dev_sol) return fail(GQ_ERR_STATE, "buffers not attached");
+  return copy(b->dev_sol, b->host_sol, b->sizes.sol_bytes, cudaMemcpyHostToDevice, stream, "upload_sol");
+}
+
+int gq_download(gq_batch* b, void* stream) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (!b->host_sol || !b->dev_sol) return fail(GQ_ERR_STATE, "buffers not attached");
+  return copy(b->host_sol, b->dev_sol, b->sizes.sol_bytes, cudaMemcpyDeviceToHost, stream, "download");
+}
+
+static int make_kernel_batch(gq_batch* b, Batch* k) {
+  if (!b->dev_in || !b->dev_sol || !b->dev_ws) return fail(GQ_ERR_STATE, "device buffers not attached");
+  char* in = static_cast<char*>(b->dev_in);
+  char* so = static_cast<char*>(b->dev_sol);
+  char* ws = static_cast<char*>(b->dev_ws);
+  const Layout& L = b->L;
+  k->nqp = b->nqp;
+  k->nvmax = b->sizes.nv_max;
+  k->nxmax = b->sizes.nx_max;
+  k->ngmax = b->ngmax;
+  k->qp = reinterpret_cast<const QpDesc*>(in + L.qpdesc);
+  k->st = reinterpret_cast<const StageDesc*>(in + L.stagedesc);
+  k->order = reinterpret_cast<const int32_t*>(in + L.order);
+  k->idx = reinterpret_cast<const int32_t*>(in + L.idx);
+  k->data = reinterpret_cast<const double*>(in + L.data);
+  k->stats = reinterpret_cast<gq_stats*>(so + L.stats);
+  k->y = reinterpret_cast<double*>(so + L.y);
+  k->pi = reinterpret_cast<double*>(so + L.pi);
+  k->lam = reinterpret_cast<double*>(so + L.lam);
+  k->t = reinterpret_cast<double*>(so + L.t);
+  double** w[] = {&k->rg, &k->rb, &k->rd, &k->rm, &k->gt, &k->dy, &k->dpi, &k->dlam, &k->dt, &k->lp,
+                  &k->rg2, &k->rb2, &k->dy2, &k->dpi2};
+  const int64_t off[] = {L.rg, L.rb, L.rd, L.rm, L.gt, L.dy, L.dpi, L.dlam, L.dt, L.lp,
+                         L.rg2, L.rb2, L.dy2, L.dpi2};
+  for (int i = 0; i < 14; ++i) *w[i] = reinterpret_cast<double*>(ws + off[i]);
+  k->fac = ws + L.fac;
+  const size_t smem = ipm_smem_bytes(*k, b->shape);
+  if (smem > kMaxSmem)
+    return fail(GQ_ERR_DIMS, "largest stage (nu+nx=%d, nx=%d) needs %zu bytes of shared memory per block (limit %zu)",
+                k->nvmax, k->nxmax, smem, kMaxSmem);
+  return GQ_OK;
+}
+
+static int check_arg(const gq_ipm_arg* a) {
+  if (a == nullptr) return fail(GQ_ERR_ARG, "arg is NULL");
+  if (a->mode != GQ_MODE_SPEED && a->mode != GQ_MODE_BALANCE) return fail(GQ_ERR_ARG, "unknown mode");
+  if (a->precision != GQ_PREC_FP64 && a->precision != GQ_PREC_MIXED) return fail(GQ_ERR_ARG, "unknown precision");
+  if (a->iter_max < 0 || a->ir_steps < 0 || a->ir_steps > 64) return fail(GQ_ERR_ARG, "iter_max/ir_steps out of range");
+  if (a->warm_start < 0 || a->warm_start > 2) return fail(GQ_ERR_ARG, "warm_start must be 0, 1 or 2");
+  if (!(a->tau_b > 0.0 && a->tau_b <= 1.0)) return fail(GQ_ERR_ARG, "tau_b must be in (0, 1]");
+  if (!(a->lam_min > 0.0 && a->t_min > 0.0)) return fail(GQ_ERR_ARG, "lam_min and t_min must be positive");
+  if (!(a->reg_prim >= 0.0)) return fail(GQ_ERR_ARG, "reg_prim must be >= 0");
+  if (a->timeout_ns < 0) return fail(GQ_ERR_ARG, "timeout_ns must be >= 0");
+  return GQ_OK;
+}
+
+int gq_solve(gq_batch* b, const gq_ipm_arg* arg, void* stream) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  rc = check_arg(arg);
+  if (rc) return rc;
+  Batch k;
+  rc = make_kernel_batch(b, &k);
+  if (rc) return rc;
+  cudaError_t e = launch_ipm(k, b->shape, *arg, static_cast<cudaStream_t>(stream), LaunchKind::Solve, 0.0, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "solve launch");
+  return GQ_OK;
+}
+
+int gq_residuals(gq_batch* b, void* stream) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  Batch k;
+  rc = make_kernel_batch(b, &k);
+  if (rc) return rc;
+  gq_ipm_arg a;
+  gq_ipm_arg_default(&a, GQ_MODE_SPEED, GQ_PREC_FP64);
+  cudaError_t e = launch_ipm(k, b->shape, a, static_cast<cudaStream_t>(stream), LaunchKind::Residuals, 0.0, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "residual launch");
+  return GQ_OK;
+}
+
+int gq_newton_step(gq_batch* b, const gq_ipm_arg* arg, double sigma_mu, void* dev_dir, void* stream) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  rc = check_arg(arg);
+  if (rc) return rc;
+  if (dev_dir == nullptr || reinterpret_cast<uintptr_t>(dev_dir) % 256)
+    return fail(GQ_ERR_ARG, "dev_dir must be non-NULL and 256-byte aligned");
+  if (!std::isfinite(sigma_mu) || sigma_mu < 0) return fail(GQ_ERR_ARG, "sigma_mu must be finite and >= 0");
+  Batch k;
+  rc = make_kernel_batch(b, &k);
+  if (rc) return rc;
+  char* d = static_cast<char*>(dev_dir);
+  DirOut out;
+  out.dy = reinterpret_cast<double*>(d + b->L.y);
+  out.dpi = reinterpret_cast<double*>(d + b->L.pi);
+  out.dlam = reinterpret_cast<double*>(d + b->L.lam);
+  out.dt = reinterpret_cast<double*>(d + b->L.t);
+  cudaError_t e = launch_ipm(k, b->shape, *arg, static_cast<cudaStream_t>(stream), LaunchKind::NewtonStep, sigma_mu, &out);
+  if (e != cudaSuccess) return cuda_fail(e, "newton-step launch");
+  return GQ_OK;
+}
+
+int gq_get_stage_sol(const gq_batch* b, int qp, int n, double* u, double* x, double* pi, double* lam,
+                     double* t) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (qp < 0 || qp >= b->nqp) return fail(GQ_ERR_ARG, "qp out of range");
+  const QpDesc& d = b->qp[qp];
+  if (n < 0 || n > d.N) return fail(GQ_ERR_ARG, "stage out of range");
+  if (b->host_sol == nullptr) return fail(GQ_ERR_STATE, "host_sol not attached");
+  const StageDesc& s = b->st[d.stage0 + n];
+  const char* h = static_cast<const char*>(b->host_sol);
+  const double* Y = reinterpret_cast<const double*>(h + b->L.y) + s.var;
+  if (u) std::memcpy(u, Y, 8 * (size_t)s.nu);
+  if (x) std::memcpy(x, Y + s.nu, 8 * (size_t)s.nx);
+  if (pi && n < d.N) std::memcpy(pi, reinterpret_cast<const double*>(h + b->L.pi) + s.eq, 8 * (size_t)s.nx1);
+  const int ns = 2 * (s.nbu + s.nbx + s.ng);
+  if (lam) std::memcpy(lam, reinterpret_cast<const double*>(h + b->L.lam) + s.side, 8 * (size_t)ns);
+  if (t) std::memcpy(t, reinterpret_cast<const double*>(h + b->L.t) + s.side, 8 * (size_t)ns);
+  return GQ_OK;
+}
+
+int gq_get_stats(const gq_batch* b, int qp, gq_stats* out) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (qp < 0 || qp >= b->nqp || out == nullptr) return fail(GQ_ERR_ARG, "qp out of range or out NULL");
+  if (b->host_sol == nullptr) return fail(GQ_ERR_STATE, "host_sol not attached");
+  const char* h = static_cast<const char*>(b->host_sol);
+  std::memcpy(out, h + b->L.stats + (int64_t)qp * sizeof(gq_stats), sizeof(gq_stats));
+  return GQ_OK;
+}
+
+int gq_get_sol_offsets(const gq_batch* b, int qp, int64_t off[8]) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (qp < 0 || qp >= b->nqp || off == nullptr) return fail(GQ_ERR_ARG, "qp out of range or off NULL");
+  const QpDesc& d = b->qp[qp];
+  off[0] = b->L.y / 8 + d.var0;
+  off[1] = b->L.pi / 8 + d.eq0;
+  off[2] = b->L.lam / 8 + d.side0;
+  off[3] = b->L.t / 8 + d.side0;
+  off[4] = d.nvt;
+  off[5] = d.neqt;
+  off[6] = d.nsidet;
+  off[7] = d.nsidet;
+  return GQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,289 @@
+"""CUDA path against the CPU oracle, through the C ABI (GPU required).
+
+Tolerances (stated here, used below):
+* FP64 row-level checks (residuals, one Newton direction): relative 1e-9 of
+  the largest entry -- both sides solve the same linear system in FP64, the
+  difference is rounding order times the condition number of eq. (kkt) at a
+  moderate iterate.
+* converged solutions: KKT residual norms recomputed on the CPU <= 1e-8 (the
+  exit rule), and ||y - y*||inf / max(1, ||y*||inf) <= 1e-6 against the
+  oracle run with the SAME exit rule (same algorithm in FP64).  Against the
+  oracle run to 1e-10 the distance is bounded by 1e-4: stopping at KKT 1e-8
+  leaves weakly active bounds with t ~ mu / lambda, which on the ragged
+  workload moves the solution by up to ~5e-5.
+* iterates after k IPM iterations (FP64): relative 1e-8.
+* mixed path: same gates as FP64 after refinement.
+"""
+import numpy as np
+import pytest
+
+import test_oracle_pins as P
+from oracle import ocp_ipm as O
+from paper_2003_02547_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SOL_TOL = 1e-6
+EXACT_TOL = 1e-4
+KKT_TOL = 1e-8
+SAME_RULE = dict(tol_stat=1e-8, tol_eq=1e-8, tol_ineq=1e-8, tol_comp=1e-8)
+
+
+def oracle_pair(qp):
+    """(same-exit-rule oracle, tightly converged oracle) solutions."""
+    return O.solve(qp, O.IpmArg(**SAME_RULE)), O.solve(qp)
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2003_02547_gb300 import build
+    build.build()
+    from paper_2003_02547_gb300 import gq
+    from paper_2003_02547_gb300.batch import QpBatch
+    return gq, QpBatch, torch
+
+
+def solve_gpu(env, qps, precision=0, mode=0, share=True, **argover):
+    gq, QpBatch, torch = env
+    b = QpBatch(qps, share=share)
+    arg = gq.default_arg(mode, precision, **argover)
+    b.upload()
+    b.solve(arg)
+    b.download()
+    torch.cuda.synchronize()
+    return b
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b), initial=0.0) / max(1.0, np.max(np.abs(b), initial=0.0)))
+
+
+def mixed_set():
+    """Stage-varying sizes, S != 0, nx_0 > 0, general rows, masked sides."""
+    out = []
+    for seed in range(4):
+        qp = P.random_lq(300 + seed, N=6, boxes=True, ng=2, tight=0.8)
+        qp.lbu[2] = np.full(len(qp.lbu[2]), -np.inf)
+        qp.ug[3] = np.full(len(qp.ug[3]), np.inf)
+        qp.validate()
+        out.append(qp)
+    return out
+
+
+def random_iterate(qp, dq, seed):
+    rng = np.random.default_rng(seed)
+    y = rng.standard_normal(dq.ny)
+    pi = rng.standard_normal(dq.neq)
+    lam = rng.uniform(0.2, 2.0, dq.nside)
+    t = rng.uniform(0.2, 2.0, dq.nside)
+    lam[~dq.active] = 0.0
+    t[~dq.active] = 1.0
+    return y, pi, lam, t
+
+
+# ----------------------------------------------------------------------------
+# a1: residuals
+# ----------------------------------------------------------------------------
+def test_residual_norms_match_oracle(env):
+    gq, QpBatch, torch = env
+    qps = mixed_set() + [W.small_random_qp(0), W.mass_spring_qp(0)]
+    b = QpBatch(qps)
+    its = []
+    for i, qp in enumerate(qps):
+        dq = O.assemble(qp)
+        it = random_iterate(qp, dq, i)
+        its.append((dq, it))
+        b.set_guess(i, *it)
+    b.upload()
+    b.upload_sol()
+    b.residuals()
+    b.download()
+    torch.cuda.synchronize()
+    st = b.all_stats()
+    for i, (dq, (y, pi, lam, t)) in enumerate(its):
+        rg, rb, rd, mu = O.residuals(dq, y, pi, lam[dq.active], t[dq.active])
+        ref = [np.max(np.abs(rg)), np.max(np.abs(rb), initial=0), np.max(np.abs(rd)), mu]
+        np.testing.assert_allclose(st["res"][i], ref, rtol=1e-12, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# a2-a4: one Newton direction through the Riccati factorisation
+# ----------------------------------------------------------------------------
+def _newton_compare(env, qps, precision, ir_steps, tol, sigma_mu=0.37):
+    gq, QpBatch, torch = env
+    b = QpBatch(qps)
+    its = []
+    for i, qp in enumerate(qps):
+        dq = O.assemble(qp)
+        it = random_iterate(qp, dq, 100 + i)
+        its.append((dq, it))
+        b.set_guess(i, *it)
+    b.upload()
+    b.upload_sol()
+    out = torch.zeros_like(b.dev_sol)
+    arg = gq.default_arg(0, precision, ir_steps=ir_steps)
+    b.newton_step(arg, sigma_mu, out)
+    torch.cuda.synchronize()
+    buf = out.cpu().numpy().view(np.float64)
+    worst = 0.0
+    for i, (dq, (y, pi, lam, t)) in enumerate(its):
+        a = dq.active
+        dy, dpi, dlam, dt = O.newton_step(dq, y, pi, lam[a], t[a], sigma_mu=sigma_mu)
+        gy, gpi, glam, gt = b.solution(i, buf)
+        for g, r in ((gy, dy), (gpi, dpi), (glam[a], dlam), (gt[a], dt)):
+            worst = max(worst, float(np.max(np.abs(g - r), initial=0) / max(1e-300, np.max(np.abs(r), initial=1))))
+        assert np.all(glam[~a] == 0.0) and np.all(gt[~a] == 0.0)
+    assert worst <= tol, worst
+    return worst
+
+
+def test_newton_step_fp64_matches_oracle(env):
+    qps = mixed_set() + [W.small_random_qp(1), W.mass_spring_qp(1), W.ragged_random_qp(5)]
+    _newton_compare(env, qps, precision=0, ir_steps=0, tol=1e-9)
+
+
+def test_newton_step_mixed_without_refinement_is_fp32_accurate(env):
+    qps = [W.small_random_qp(1), W.mass_spring_qp(1)]
+    w = _newton_compare(env, qps, precision=1, ir_steps=0, tol=1e-3)
+    assert w > 1e-12   # it really ran in FP32
+
+
+def test_newton_step_mixed_with_refinement_matches_oracle(env):
+    qps = [W.small_random_qp(1), W.mass_spring_qp(1)] + mixed_set()[:2]
+    _newton_compare(env, qps, precision=1, ir_steps=4, tol=1e-9)
+
+
+# ----------------------------------------------------------------------------
+# full IPM
+# ----------------------------------------------------------------------------
+def _check_converged(b, qps, refs, sol_tol=SOL_TOL):
+    """refs[i] is None or a pair from oracle_pair()."""
+    st = b.all_stats()
+    for i, qp in enumerate(qps):
+        assert st["status"][i] == 0, (i, st[i])
+        y, pi, lam, t = b.solution(i)
+        kkt = O.full_residuals(qp, y, pi, lam, t)
+        assert max(kkt[:4]) <= KKT_TOL * 1.01, (i, kkt)
+        assert np.all(lam >= 0) and np.all(t > 0)
+        if refs is not None and refs[i] is not None:
+            same, tight = refs[i]
+            assert same.status == O.CONVERGED and tight.status == O.CONVERGED
+            assert rel_err(y, same.y) <= sol_tol, (i, rel_err(y, same.y), st["iters"][i], same.iters)
+            assert rel_err(y, tight.y) <= EXACT_TOL, (i, rel_err(y, tight.y))
+
+
+def test_ipm_fp64_matches_oracle_small(env):
+    qps = [W.small_random_qp(i) for i in range(4)] + mixed_set()
+    refs = [oracle_pair(q) for q in qps]
+    b = solve_gpu(env, qps, precision=0)
+    _check_converged(b, qps, refs)
+
+
+def test_ipm_fp64_matches_oracle_ragged(env):
+    qps = [W.ragged_random_qp(i) for i in range(3)]
+    refs = [oracle_pair(q) for q in qps]
+    b = solve_gpu(env, qps, precision=0)
+    _check_converged(b, qps, refs)
+
+
+def test_ipm_iterates_match_oracle(env):
+    """Same algorithm step by step: iterates after k iterations agree."""
+    qps = [W.small_random_qp(2), W.mass_spring_qp(2)] + mixed_set()[:2]
+    for k in (1, 2, 3):
+        b = solve_gpu(env, qps, precision=0, iter_max=k, tol_stat=0.0, tol_eq=0.0, tol_ineq=0.0, tol_comp=0.0)
+        for i, qp in enumerate(qps):
+            ref = O.solve(qp, O.IpmArg(iter_max=k, tol_stat=0, tol_eq=0, tol_ineq=0, tol_comp=0))
+            y, pi, lam, t = b.solution(i)
+            assert b.all_stats()["iters"][i] == k
+            assert rel_err(y, ref.y) <= 1e-8, (k, i)
+            assert rel_err(pi, ref.pi) <= 1e-8, (k, i)
+            assert rel_err(lam, ref.lam) <= 1e-8, (k, i)
+            assert rel_err(t, ref.t) <= 1e-8, (k, i)
+
+
+def test_ipm_mixed_matches_oracle(env):
+    qps = [W.small_random_qp(0)] + [W.mass_spring_qp(i) for i in range(6)] + mixed_set()[:2]
+    refs = [oracle_pair(q) for q in qps]
+    b = solve_gpu(env, qps, precision=1)
+    _check_converged(b, qps, refs)
+
+
+def test_unconstrained_is_one_newton_step(env):
+    qps = [P.random_lq(s, N=6) for s in range(3)]
+    b = solve_gpu(env, qps, precision=0)
+    st = b.all_stats()
+    for i, qp in enumerate(qps):
+        assert st["status"][i] == 0 and st["iters"][i] == 1
+        us, xs, pis = P.riccati_dp(qp)
+        y, pi, _, _ = b.solution(i)
+        ref = np.concatenate([np.concatenate([us[n], xs[n]]) for n in range(qp.N + 1)])
+        np.testing.assert_allclose(y, ref, rtol=1e-9, atol=1e-10)
+        np.testing.assert_allclose(pi, np.concatenate(pis), rtol=1e-9, atol=1e-10)
+
+
+def test_batch_invariance_bitwise(env):
+    """A QP gives the same bits alone and inside a ragged batch."""
+    target = W.mass_spring_qp(7)
+    mix = [W.ragged_random_qp(i) for i in range(4)] + [target] + [W.small_random_qp(3)]
+    for prec in (0, 1):
+        alone = solve_gpu(env, [target], precision=prec)
+        inmix = solve_gpu(env, mix, precision=prec)
+        for a, b_ in zip(alone.solution(0), inmix.solution(4)):
+            np.testing.assert_array_equal(a, b_)
+        assert alone.all_stats()["iters"][0] == inmix.all_stats()["iters"][4]
+
+
+def test_status_paths_do_not_poison_neighbours(env):
+    gq, QpBatch, torch = env
+    good = W.small_random_qp(0)
+    rng = np.random.default_rng([7, 7])
+    bad = P.random_lq(107, N=2, nxs=[0, 2, 2], nus=[1, 1, 0], boxes=True, tight=0.35)
+    bad.idxbx[2] = bad.idxbx[2][:1]
+    bad.lbx[2] = bad.lbx[2][:1]
+    bad.ubx[2] = bad.ubx[2][:1]
+    bad.C[1] = rng.standard_normal((1, 2))
+    bad.D[1] = rng.standard_normal((1, 1))
+    bad.lg[1] = np.array([-0.3])
+    bad.ug[1] = np.array([0.4])
+    assert P.brute_force(bad) is None          # infeasible
+    b = solve_gpu(env, [good, bad, good], precision=0, iter_max=60)
+    st = b.all_stats()
+    assert st["status"][0] == 0 and st["status"][2] == 0
+    assert st["status"][1] in (1, 2, 3)
+    np.testing.assert_array_equal(b.solution(0)[0], b.solution(2)[0])
+    # iteration cap and device timeout end every QP with its own status
+    b = solve_gpu(env, [good], precision=0, iter_max=0)
+    assert b.all_stats()["status"][0] == 1
+    b = solve_gpu(env, [good, W.mass_spring_qp(0)], precision=0, timeout_ns=1)
+    assert list(b.all_stats()["status"]) == [4, 4]
+
+
+def test_warm_start_converges_faster(env):
+    gq, QpBatch, torch = env
+    qp = W.ragged_random_qp(11)
+    cold = solve_gpu(env, [qp], precision=0)
+    y, pi, lam, t = cold.solution(0)
+    qp2 = W.perturb_x0(qp, qp.x0 + 0.01 * np.random.default_rng(0).standard_normal(qp.x0.shape))
+    b = QpBatch([qp2])
+    b.set_guess(0, y, pi, lam, t)
+    b.upload()
+    b.upload_sol()
+    b.solve(gq.default_arg(0, 0, warm_start=2))
+    b.download()
+    torch.cuda.synchronize()
+    _check_converged(b, [qp2], [oracle_pair(qp2)])
+    assert b.all_stats()["iters"][0] < cold.all_stats()["iters"][0]
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_mass_spring_full_batch(env, precision):
+    """The timed workload: 1024 mass-spring QPs, one launch.  Every QP is
+    checked through KKT residuals recomputed on the CPU; a sample against
+    the oracle's solution."""
+    qps = W.mass_spring_batch(1024)
+    b = solve_gpu(env, qps, precision=precision)
+    sample = set(range(0, 1024, 97)) | {1023}
+    refs = [oracle_pair(q) if i in sample else None for i, q in enumerate(qps)]
+    _check_converged(b, qps, refs)
