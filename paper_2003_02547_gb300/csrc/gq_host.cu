@@ -39,7 +39,7 @@ struct SlotEntry {
   int64_t key;    // slot id, -1 = empty
   int64_t block;  // data offset (doubles)
   int32_t stage;  // first stage using this slot
-  int32_t idx;    // box-index offset (ints), shared like the data block
+  int32_t pad;
 };
 
 }  // namespace
@@ -51,10 +51,12 @@ struct gq_batch {
   Layout L;
   gq_sizes sizes;
   int32_t ngmax;
-  Shape shape;
+  int32_t nwarp;        // QPs run one per warp; they lead the order array
+  Shape shape_w, shape_b;
   QpDesc* qp;
   StageDesc* st;
   int32_t* order;
+  int32_t* slot_stage;  // first stage of every distinct data block
   SlotEntry* hash;
   void *host_in, *host_sol, *dev_in, *dev_sol, *dev_ws;
 };
@@ -124,15 +126,13 @@ size_t handle_bytes(int nqp, int64_t n_stages, int64_t cap) {
   b += align_up((int64_t)nqp * sizeof(QpDesc), 64);
   b += align_up(n_stages * sizeof(StageDesc), 64);
   b += align_up((int64_t)nqp * sizeof(int32_t), 64);
+  b += align_up(n_stages * sizeof(int32_t), 64);
   b += align_up(cap * sizeof(SlotEntry), 64);
   return (size_t)b;
 }
 
 inline double* host_data(gq_batch* b) {
   return reinterpret_cast<double*>(static_cast<char*>(b->host_in) + b->L.data);
-}
-inline int32_t* host_idx(gq_batch* b) {
-  return reinterpret_cast<int32_t*>(static_cast<char*>(b->host_in) + b->L.idx);
 }
 
 int check_batch(const gq_batch* b) {
@@ -217,6 +217,8 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
   p += align_up(c.n_stages * sizeof(StageDesc), 64);
   b->order = reinterpret_cast<int32_t*>(p);
   p += align_up((int64_t)nqp * sizeof(int32_t), 64);
+  b->slot_stage = reinterpret_cast<int32_t*>(p);
+  p += align_up(c.n_stages * sizeof(int32_t), 64);
   b->hash = reinterpret_cast<SlotEntry*>(p);
   b->hash_cap = cap;
   for (int64_t i = 0; i < cap; ++i) b->hash[i].key = -1;
@@ -224,8 +226,9 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
   b->n_stages = c.n_stages;
 
   // walk the dims: stage descriptors, vector offsets, data blocks
-  int64_t var = 0, eq = 0, side = 0, idx = 0, data = 0, fac = 0, slots = 0;
+  int64_t var = 0, eq = 0, side = 0, data = 0, fac = 0, slots = 0;
   int nvmax = 0, nxmax = 0, ngmax = 0, nstmax = 0, nemax = 0, nsidemax = 0;
+  int64_t datamax = 0;
   size_t pos = 0;
   int64_t si = 0;
   for (int q = 0; q < nqp; ++q) {
@@ -256,7 +259,7 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
       var += nv;
       eq += s.nx1;
       side += 2 * nc;
-      fac += (int64_t)nv * nv;
+      fac += fac_block_elems(nv);
       nvmax = std::max(nvmax, nv);
       nxmax = std::max(nxmax, s.nx);
       nemax = std::max(nemax, n == 0 ? nv : s.nu);
@@ -266,13 +269,13 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
       cost += (double)s.nx1 * s.nx1 * nv + (double)s.nx1 * nv * nv + (double)nv * nv * nv / 3.0 +
               (double)s.ng * nv * nv;
       const StageData lay = stage_data_layout(s.nx, s.nu, s.nx1, nb, s.ng);
+      datamax = std::max(datamax, lay.size);
       const int slot = stage_slot ? stage_slot[si] : -1;
+      s.idx = 0;
       if (slot < 0) {
         s.data = data;
-        s.idx = (int32_t)idx;
         data += lay.size;
-        idx += nb;
-        ++slots;
+        b->slot_stage[slots++] = (int32_t)si;
       } else {
         int64_t h = ((uint64_t)slot * 0x9E3779B97F4A7C15ull) & (cap - 1);
         while (b->hash[h].key != -1 && b->hash[h].key != slot) h = (h + 1) & (cap - 1);
@@ -280,12 +283,9 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
           b->hash[h].key = slot;
           b->hash[h].block = data;
           b->hash[h].stage = (int32_t)si;
-          b->hash[h].idx = (int32_t)idx;
           s.data = data;
-          s.idx = (int32_t)idx;
           data += lay.size;
-          idx += nb;
-          ++slots;
+          b->slot_stage[slots++] = (int32_t)si;
         } else {
           const StageDesc& f = b->st[b->hash[h].stage];
           if (f.nx != s.nx || f.nu != s.nu || f.nx1 != s.nx1 || f.nbx != s.nbx || f.nbu != s.nbu ||
@@ -293,7 +293,6 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
             return fail(GQ_ERR_DIMS, "QP %d stage %d shares slot %d with a stage of other sizes", q, n,
                         slot);
           s.data = b->hash[h].block;
-          s.idx = b->hash[h].idx;
         }
       }
     }
@@ -304,14 +303,42 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
     d.cost = cost;
     nsidemax = std::max(nsidemax, d.nsidet);
   }
-  if (var >= INT32_MAX || eq >= INT32_MAX || side >= INT32_MAX || idx >= INT32_MAX)
+  if (var >= INT32_MAX || eq >= INT32_MAX || side >= INT32_MAX)
     return fail(GQ_ERR_DIMS, "batch too large for 32-bit vector offsets");
 
-  // longest-processing-time order: most expensive QPs launch first
-  for (int q = 0; q < nqp; ++q) b->order[q] = q;
+  // buckets: QPs whose stages fit one warp first, then the rest; each bucket
+  // in longest-processing-time order (most expensive QPs launch first)
   QpDesc* qd = b->qp;
-  std::stable_sort(b->order, b->order + nqp,
-                   [qd](int32_t a, int32_t c2) { return qd[a].cost > qd[c2].cost; });
+  auto warp_ok = [&](int q) { return qd[q].nvmax <= kWarpMaxNv && qd[q].nxmax <= kWarpMaxNv; };
+  int nw = 0;
+  for (int q = 0; q < nqp; ++q)
+    if (warp_ok(q)) b->order[nw++] = q;
+  int nb_ = nw;
+  for (int q = 0; q < nqp; ++q)
+    if (!warp_ok(q)) b->order[nb_++] = q;
+  auto by_cost = [qd](int32_t a, int32_t c2) { return qd[a].cost > qd[c2].cost; };
+  std::stable_sort(b->order, b->order + nw, by_cost);
+  std::stable_sort(b->order + nw, b->order + nqp, by_cost);
+  b->nwarp = nw;
+  for (int bucket = 0; bucket < 2; ++bucket) {
+    Shape& sh = bucket == 0 ? b->shape_w : b->shape_b;
+    std::memset(&sh, 0, sizeof(sh));
+    const int lo = bucket == 0 ? 0 : nw, hi = bucket == 0 ? nw : nqp;
+    for (int k = lo; k < hi; ++k) {
+      const QpDesc& d = qd[b->order[k]];
+      sh.nst_max = std::max(sh.nst_max, d.N + 1);
+      sh.nside_max = std::max(sh.nside_max, d.nsidet);
+      for (int n = 0; n <= d.N; ++n) {
+        const StageDesc& st = b->st[d.stage0 + n];
+        const int nv = st.nx + st.nu;
+        sh.nvmax = std::max(sh.nvmax, nv);
+        sh.nxmax = std::max(sh.nxmax, st.nx);
+        sh.ngmax = std::max(sh.ngmax, st.ng);
+        sh.ne_max = std::max(sh.ne_max, n == 0 ? nv : st.nu);
+        sh.data_max = std::max(sh.data_max, stage_data_layout(st.nx, st.nu, st.nx1, st.nbu + st.nbx, st.ng).size);
+      }
+    }
+  }
 
   Layout& L = b->L;
   int64_t o = 0;
@@ -321,8 +348,8 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
   o = align_up(o + c.n_stages * sizeof(StageDesc), 256);
   L.order = o;
   o = align_up(o + (int64_t)nqp * 4, 256);
-  L.idx = o;
-  o = align_up(o + idx * 4, 256);
+  L.slots = o;
+  o = align_up(o + slots * 4, 256);
   L.data = o;
   o = align_up(o + data * 8, 256);
   L.in_bytes = o;
@@ -342,14 +369,16 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
 
   o = 0;
   int64_t* vecs[] = {&L.rg, &L.rb, &L.rd, &L.rm, &L.gt, &L.dy, &L.dpi, &L.dlam, &L.dt, &L.lp,
-                     &L.rg2, &L.rb2, &L.dy2, &L.dpi2};
-  const int64_t lens[] = {var, eq, side, side, var, var, eq, side, side, var, var, eq, var, eq};
-  for (int i = 0; i < 14; ++i) {
+                     &L.rg2, &L.rb2, &L.dy2, &L.dpi2, &L.dlam2, &L.dt2, &L.tinv};
+  const int64_t lens[] = {var, eq, side, side, var, var, eq, side, side, var, var, eq, var, eq, side, side, side};
+  for (int i = 0; i < 17; ++i) {
     *vecs[i] = o;
     o = align_up(o + lens[i] * 8, 256);
   }
   L.fac = o;
   o = align_up(o + fac * 8, 256);
+  L.data32 = o;
+  o = align_up(o + data * 4, 256);
   L.ws_bytes = o;
 
   gq_sizes& z = b->sizes;
@@ -364,9 +393,10 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
   z.nv_max = nvmax;
   z.nx_max = nxmax;
   b->ngmax = ngmax;
-  b->shape.nst_max = nstmax;
-  b->shape.ne_max = nemax;
-  b->shape.nside_max = nsidemax;
+  (void)nstmax;
+  (void)nemax;
+  (void)nsidemax;
+  (void)datamax;
   b->n_slots = slots;
   b->magic = kMagic;
   *out = b;
@@ -398,10 +428,11 @@ int gq_batch_attach(gq_batch* b, void* host_in, void* host_sol, void* dev_in, vo
   b->dev_ws = dev_ws;
   if (host_in) {
     char* h = static_cast<char*>(host_in);
-    std::memset(h + b->L.idx, 0, (size_t)(b->L.in_bytes - b->L.idx));
+    std::memset(h + b->L.data, 0, (size_t)(b->L.in_bytes - b->L.data));
     std::memcpy(h + b->L.qpdesc, b->qp, (size_t)b->nqp * sizeof(QpDesc));
     std::memcpy(h + b->L.stagedesc, b->st, (size_t)b->n_stages * sizeof(StageDesc));
     std::memcpy(h + b->L.order, b->order, (size_t)b->nqp * sizeof(int32_t));
+    std::memcpy(h + b->L.slots, b->slot_stage, (size_t)b->n_slots * sizeof(int32_t));
   }
   return GQ_OK;
 }
@@ -419,11 +450,11 @@ int gq_set_dynamics(gq_batch* b, int qp, int n, const double* A, int lda, const 
   const StageData lay = stage_data_layout(nx, nu, nx1, s->nbu + s->nbx, s->ng);
   double* D = host_data(b) + s->data;
   for (int i = 0; i < nu; ++i)
-    for (int k = 0; k < nx1; ++k) D[lay.BAt + (int64_t)i * nx1 + k] = B[k + (int64_t)i * ldb];
+    for (int k = 0; k < nx1; ++k) D[lay.BAt + (int64_t)i * lay.ldb + k] = B[k + (int64_t)i * ldb];
   for (int i = 0; i < nx; ++i)
-    for (int k = 0; k < nx1; ++k) D[lay.BAt + (int64_t)(nu + i) * nx1 + k] = A[k + (int64_t)i * lda];
+    for (int k = 0; k < nx1; ++k) D[lay.BAt + (int64_t)(nu + i) * lay.ldb + k] = A[k + (int64_t)i * lda];
   for (int k = 0; k < nx1; ++k) D[lay.b + k] = bvec[k];
-  if (!finite_all(D + lay.BAt, (nu + nx) * nx1 + nx1)) return fail(GQ_ERR_DATA, "non-finite dynamics data");
+  if (!finite_all(D + lay.BAt, (nu + nx) * lay.ldb + nx1)) return fail(GQ_ERR_DATA, "non-finite dynamics data");
   return GQ_OK;
 }
 
@@ -451,19 +482,20 @@ int gq_set_cost(gq_batch* b, int qp, int n, const double* Q, int ldq, const doub
   const StageData lay = stage_data_layout(nx, nu, s->nx1, s->nbu + s->nbx, s->ng);
   double* D = host_data(b) + s->data;
   double* RSQ = D + lay.RSQ;
+  const int64_t lr = lay.ldr;
   for (int i = 0; i < nu; ++i)
-    for (int j = 0; j < nu; ++j) RSQ[(int64_t)i * nv + j] = R[i + (int64_t)j * ldr];
+    for (int j = 0; j < nu; ++j) RSQ[i * lr + j] = R[i + (int64_t)j * ldr];
   for (int i = 0; i < nu; ++i)
     for (int j = 0; j < nx; ++j) {
       const double v = S[i + (int64_t)j * lds];
-      RSQ[(int64_t)i * nv + nu + j] = v;
-      RSQ[(int64_t)(nu + j) * nv + i] = v;
+      RSQ[i * lr + nu + j] = v;
+      RSQ[(int64_t)(nu + j) * lr + i] = v;
     }
   for (int i = 0; i < nx; ++i)
-    for (int j = 0; j < nx; ++j) RSQ[(int64_t)(nu + i) * nv + nu + j] = Q[i + (int64_t)j * ldq];
+    for (int j = 0; j < nx; ++j) RSQ[(int64_t)(nu + i) * lr + nu + j] = Q[i + (int64_t)j * ldq];
   for (int i = 0; i < nu; ++i) D[lay.rq + i] = r[i];
   for (int i = 0; i < nx; ++i) D[lay.rq + nu + i] = q[i];
-  if (!finite_all(RSQ, nv * nv + nv)) return fail(GQ_ERR_DATA, "non-finite cost data");
+  if (!finite_all(RSQ, (int)(nv * lr + nv))) return fail(GQ_ERR_DATA, "non-finite cost data");
   return GQ_OK;
 }
 
@@ -478,7 +510,7 @@ int gq_set_box(gq_batch* b, int qp, int n, const int* idxbu, const double* lbu, 
     return fail(GQ_ERR_ARG, "box pointers must be non-NULL");
   const StageData lay = stage_data_layout(s->nx, s->nu, s->nx1, nb, s->ng);
   double* D = host_data(b) + s->data;
-  int32_t* I = host_idx(b) + s->idx;
+  int32_t* I = reinterpret_cast<int32_t*>(D + lay.box);   // bidx[nb], then bmap[nv]
   for (int k = 0; k < nbu; ++k) {
     if (idxbu[k] < 0 || idxbu[k] >= s->nu) return fail(GQ_ERR_ARG, "idxbu[%d]=%d out of range", k, idxbu[k]);
     for (int j = 0; j < k; ++j)
@@ -500,6 +532,10 @@ int gq_set_box(gq_batch* b, int qp, int n, const int* idxbu, const double* lbu, 
     if (std::isnan(lo) || std::isnan(hi) || lo > hi || lo == INFINITY || hi == -INFINITY)
       return fail(GQ_ERR_DATA, "box bound %d invalid (lo=%g hi=%g)", k, lo, hi);
   }
+  int32_t* M = I + nb;
+  const int nv = s->nx + s->nu;
+  for (int i = 0; i < nv; ++i) M[i] = -1;
+  for (int k = 0; k < nb; ++k) M[I[k]] = k;
   (void)nc;
   return GQ_OK;
 }
@@ -585,24 +621,43 @@ static int make_kernel_batch(gq_batch* b, Batch* k) {
   k->qp = reinterpret_cast<const QpDesc*>(in + L.qpdesc);
   k->st = reinterpret_cast<const StageDesc*>(in + L.stagedesc);
   k->order = reinterpret_cast<const int32_t*>(in + L.order);
-  k->idx = reinterpret_cast<const int32_t*>(in + L.idx);
+  k->slots = reinterpret_cast<const int32_t*>(in + L.slots);
+  k->nslots = (int32_t)b->n_slots;
   k->data = reinterpret_cast<const double*>(in + L.data);
+  k->data32 = reinterpret_cast<float*>(ws + L.data32);
   k->stats = reinterpret_cast<gq_stats*>(so + L.stats);
   k->y = reinterpret_cast<double*>(so + L.y);
   k->pi = reinterpret_cast<double*>(so + L.pi);
   k->lam = reinterpret_cast<double*>(so + L.lam);
   k->t = reinterpret_cast<double*>(so + L.t);
   double** w[] = {&k->rg, &k->rb, &k->rd, &k->rm, &k->gt, &k->dy, &k->dpi, &k->dlam, &k->dt, &k->lp,
-                  &k->rg2, &k->rb2, &k->dy2, &k->dpi2};
+                  &k->rg2, &k->rb2, &k->dy2, &k->dpi2, &k->dlam2, &k->dt2, &k->tinv};
   const int64_t off[] = {L.rg, L.rb, L.rd, L.rm, L.gt, L.dy, L.dpi, L.dlam, L.dt, L.lp,
-                         L.rg2, L.rb2, L.dy2, L.dpi2};
-  for (int i = 0; i < 14; ++i) *w[i] = reinterpret_cast<double*>(ws + off[i]);
+                         L.rg2, L.rb2, L.dy2, L.dpi2, L.dlam2, L.dt2, L.tinv};
+  for (int i = 0; i < 17; ++i) *w[i] = reinterpret_cast<double*>(ws + off[i]);
   k->fac = ws + L.fac;
-  const size_t smem = ipm_smem_bytes(*k, b->shape);
-  if (smem > kMaxSmem)
-    return fail(GQ_ERR_DIMS, "largest stage (nu+nx=%d, nx=%d) needs %zu bytes of shared memory per block (limit %zu)",
-                k->nvmax, k->nxmax, smem, kMaxSmem);
+  if (b->nwarp < b->nqp) {
+    const size_t smem = ipm_smem_bytes(*k, b->shape_b);
+    if (smem > kMaxSmem)
+      return fail(GQ_ERR_DIMS,
+                  "largest stage (nu+nx=%d, nx=%d) needs %zu bytes of shared memory per block (limit %zu)",
+                  b->shape_b.nvmax, b->shape_b.nxmax, smem, kMaxSmem);
+  }
+  if (b->nwarp > 0) {
+    const size_t smem = warp_plan(*k, b->shape_w, GQ_PREC_FP64).bytes;
+    if (smem > kMaxSmem)
+      return fail(GQ_ERR_DIMS, "warp bucket needs %zu bytes of shared memory per block (limit %zu)", smem, kMaxSmem);
+  }
   return GQ_OK;
+}
+
+// both buckets of the batch, in order, on one stream
+static cudaError_t launch_all(gq_batch* b, const Batch& k, const gq_ipm_arg& arg, cudaStream_t st, LaunchKind kind,
+                              double sigma_mu, const DirOut* out) {
+  const int32_t* ord = k.order;
+  cudaError_t e = launch_warp_ipm(k, b->shape_w, arg, st, kind, sigma_mu, out, ord, b->nwarp);
+  if (e != cudaSuccess) return e;
+  return launch_ipm(k, b->shape_b, arg, st, kind, sigma_mu, out, ord + b->nwarp, b->nqp - b->nwarp);
 }
 
 static int check_arg(const gq_ipm_arg* a) {
@@ -626,7 +681,7 @@ int gq_solve(gq_batch* b, const gq_ipm_arg* arg, void* stream) {
   Batch k;
   rc = make_kernel_batch(b, &k);
   if (rc) return rc;
-  cudaError_t e = launch_ipm(k, b->shape, *arg, static_cast<cudaStream_t>(stream), LaunchKind::Solve, 0.0, nullptr);
+  cudaError_t e = launch_all(b, k, *arg, static_cast<cudaStream_t>(stream), LaunchKind::Solve, 0.0, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "solve launch");
   return GQ_OK;
 }
@@ -639,7 +694,7 @@ int gq_residuals(gq_batch* b, void* stream) {
   if (rc) return rc;
   gq_ipm_arg a;
   gq_ipm_arg_default(&a, GQ_MODE_SPEED, GQ_PREC_FP64);
-  cudaError_t e = launch_ipm(k, b->shape, a, static_cast<cudaStream_t>(stream), LaunchKind::Residuals, 0.0, nullptr);
+  cudaError_t e = launch_all(b, k, a, static_cast<cudaStream_t>(stream), LaunchKind::Residuals, 0.0, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "residual launch");
   return GQ_OK;
 }
@@ -661,7 +716,7 @@ int gq_newton_step(gq_batch* b, const gq_ipm_arg* arg, double sigma_mu, void* de
   out.dpi = reinterpret_cast<double*>(d + b->L.pi);
   out.dlam = reinterpret_cast<double*>(d + b->L.lam);
   out.dt = reinterpret_cast<double*>(d + b->L.t);
-  cudaError_t e = launch_ipm(k, b->shape, *arg, static_cast<cudaStream_t>(stream), LaunchKind::NewtonStep, sigma_mu, &out);
+  cudaError_t e = launch_all(b, k, *arg, static_cast<cudaStream_t>(stream), LaunchKind::NewtonStep, sigma_mu, &out);
   if (e != cudaSuccess) return cuda_fail(e, "newton-step launch");
   return GQ_OK;
 }

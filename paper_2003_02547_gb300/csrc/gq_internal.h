@@ -29,31 +29,48 @@ struct QpDesc {
 };
 static_assert(sizeof(QpDesc) == 56, "QpDesc layout");
 
-// Stage data block (doubles), for nv = nu + nx, nc = nbu + nbx + ng:
-//   BAt  nv x nx1 row-major: row i holds column i of [B A]   (row-of-[u;x] order)
+// Stage data block (elements), for nv = nu + nx, nb = nbu + nbx, nc = nb + ng:
+//   BAt  nv x ldb row-major (ldb = nx1 rounded up to odd): row i holds
+//        column i of [B A]   (row-of-[u;x] order)
 //   b    nx1
-//   RSQ  nv x nv row-major, [[R, S], [S', Q]]
+//   RSQ  nv x ldr row-major (ldr = nv rounded up to odd), [[R, S], [S', Q]]
 //   rq   nv, [r; q]
 //   DC   ng x nv row-major, [D C]
 //   lo   nc   (box u, box x, general), -inf masks the side
 //   hi   nc
-// padded to an even number of doubles (16-byte alignment of every block).
+//   box  int32 region of nb + nv element slots: bidx[nb] (variable index of
+//        box c within [u;x]) then bmap[nv] (box index of variable i, or -1)
+// The same element layout serves the FP64 block and its FP32 mirror (the box
+// region is sized so that its int32 entries fit at either element width).
+// Odd row strides keep lane-per-row shared-memory reads free of bank
+// conflicts; blocks are padded to a multiple of four elements, so every block
+// is a multiple of 16 bytes at both widths and starts on a 16-byte boundary
+// (one bulk copy per stage).
+__host__ __device__ inline int odd_ld(int n) { return n | 1; }
 struct StageData {
-  int64_t BAt, b, RSQ, rq, DC, lo, hi, size;
+  int64_t BAt, b, RSQ, rq, DC, lo, hi, box, size;
+  int ldb, ldr;
 };
 __host__ __device__ inline StageData stage_data_layout(int nx, int nu, int nx1, int nb, int ng) {
   StageData s;
   const int64_t nv = nx + nu, nc = nb + ng;
+  s.ldb = odd_ld(nx1);
+  s.ldr = odd_ld((int)nv);
   s.BAt = 0;
-  s.b = s.BAt + nv * nx1;
+  s.b = s.BAt + nv * s.ldb;
   s.RSQ = s.b + nx1;
-  s.rq = s.RSQ + nv * nv;
+  s.rq = s.RSQ + nv * s.ldr;
   s.DC = s.rq + nv;
   s.lo = s.DC + (int64_t)ng * nv;
   s.hi = s.lo + nc;
-  s.size = (s.hi + nc + 1) & ~int64_t(1);
+  s.box = s.hi + nc;
+  s.size = (s.box + nb + nv + 3) & ~int64_t(3);
   return s;
 }
+
+// Factor block of a stage: nv x odd_ld(nv) row-major, padded to a multiple of
+// four elements so that every block starts on a 16-byte boundary (bulk copies).
+__host__ __device__ inline int64_t fac_block_elems(int nv) { return ((int64_t)nv * odd_ld(nv) + 3) & ~int64_t(3); }
 
 // Per-QP statistics at the head of the sol buffer (== gq_stats).
 static_assert(sizeof(gq_stats) == 64, "gq_stats layout");
@@ -61,24 +78,26 @@ static_assert(sizeof(gq_stats) == 64, "gq_stats layout");
 // Byte offsets of the regions of the three buffers.
 struct Layout {
   // "in" buffer
-  int64_t qpdesc, stagedesc, order, idx, data, in_bytes;
+  int64_t qpdesc, stagedesc, order, slots, data, in_bytes;
   // "sol" buffer
   int64_t stats, y, pi, lam, t, sol_bytes;
   // workspace: FP64 vectors then the factor arena
-  int64_t rg, rb, rd, rm, gt, dy, dpi, dlam, dt, lp, rg2, rb2, dy2, dpi2, fac, ws_bytes;
+  int64_t rg, rb, rd, rm, gt, dy, dpi, dlam, dt, lp, rg2, rb2, dy2, dpi2, dlam2, dt2, tinv, fac, data32, ws_bytes;
 };
 
 // Kernel launch parameters (passed by value).
 struct Batch {
   int32_t nqp, nvmax, nxmax, ngmax;
+  int32_t nslots, pad;
   const QpDesc* qp;
   const StageDesc* st;
   const int32_t* order;
-  const int32_t* idx;
+  const int32_t* slots;   // one stage index per distinct data block
   const double* data;
+  float* data32;          // FP32 mirror of `data` (same element layout)
   gq_stats* stats;
   double *y, *pi, *lam, *t;
-  double *rg, *rb, *rd, *rm, *gt, *dy, *dpi, *dlam, *dt, *lp, *rg2, *rb2, *dy2, *dpi2;
+  double *rg, *rb, *rd, *rm, *gt, *dy, *dpi, *dlam, *dt, *lp, *rg2, *rb2, *dy2, *dpi2, *dlam2, *dt2, *tinv;
   void* fac;
 };
 

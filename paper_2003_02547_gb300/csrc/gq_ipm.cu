@@ -2,15 +2,22 @@
 //
 // One thread block solves one QP: the whole Mehrotra predictor-corrector loop
 // (Sec. 4.2) runs on the device, with
-//   a1  residuals of eq. (delta)                              FP64
-//   a2  barrier terms and the reduced right-hand side, eq. (kkt) FP64
-//   a3  square-root Riccati factorisation (Sec. 3.3, variant b) Tf
-//   a4  Riccati solve: backward vector sweep, forward sweep      Tf
-//   a5  affine step length and duality measure                  FP64
-//   a6  Mehrotra corrector, conditional (Sec. 4.2)               Tf solve
-//   a7  iterative refinement on eq. (itref) (Sec. 3.4)           FP64 residual
-//   a8  step, update, lower clamp of lambda and t (Sec. 4.2)     FP64
+//   a1  residuals of eq. (delta)                                 FP64
+//   a2  barrier terms and the reduced right-hand side, eq. (kkt)  FP64
+//   a3  square-root Riccati factorisation (Sec. 3.3, variant b)   Tf
+//   a4  Riccati solve: backward vector sweep, forward sweep        Tf
+//   a5  affine step length and duality measure                    FP64
+//   a6  Mehrotra corrector, conditional (Sec. 4.2)                 Tf solve
+//   a7  iterative refinement on eq. (itref) (Sec. 3.4)             FP64 residual
+//   a8  step, update, lower clamp of lambda and t (Sec. 4.2)       FP64
 // Tf is double (plain path) or float (mixed path).
+//
+// Data movement.  Every phase walks the stages of its QP in order ("sweep").
+// A sweep stages each stage's data block -- and in the solves its factor
+// block -- into shared memory with one 1-D bulk copy (cp.async.bulk, the TMA
+// unit) into a two-slot ring on mbarriers: stage n+-1 is in flight while
+// stage n is computed, and every inner loop reads shared memory.  Stages too
+// large for the ring are read from global memory by the same code.
 //
 // Riccati recursion used here.  The reduced system eq. (kkt) is the KKT system
 // of an equality-constrained LQ problem with stage Hessians Ht_n = RSQ_n +
@@ -31,26 +38,55 @@
 
 #include <cstdint>
 
+#include "gq_device.h"
 #include "gq_internal.h"
 #include "gq_launch.h"
 
 namespace gq {
-namespace {
 
-constexpr double kIrFailRatio = 1e-6;  // mixed path: IR residual ratio that triggers FP64 factors
-
-__device__ __forceinline__ int64_t globaltimer() {
-  int64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
+__host__ __device__ SmemPlan smem_plan(const Batch& b, const Shape& sh) {
+  SmemPlan p;
+  size_t o = 0;
+  auto take = [&](size_t bytes, size_t align) {
+    o = (o + align - 1) / align * align;
+    const size_t at = o;
+    o += bytes;
+    return at;
+  };
+  p.vmax = sh.nvmax + sh.ngmax + 2;
+  p.bars = take(2 * sizeof(uint64_t) + 16, 16);  // two mbarriers, then an int counter
+  p.red = take(32 * sizeof(double), 16);
+  p.chunk = take((size_t)((sh.nside_max + 31) / 32 + 1) * sizeof(double), 16);
+  p.vec = take((size_t)8 * p.vmax * sizeof(double), 16);
+  const int wide = sh.nxmax > sh.ne_max ? sh.nxmax : sh.ne_max;
+  p.mat = take(((size_t)sh.nxmax * sh.nxmax + (size_t)sh.nvmax * sh.nvmax + (size_t)sh.nvmax * (wide > 0 ? wide : 1)) *
+                   sizeof(double),
+               16);
+  p.stages = take((size_t)sh.nst_max * sizeof(StageDesc), 16);
+  // ring: two buffers of (data block + FP64-sized factor block)
+  p.ring_fac = (size_t)((sh.data_max * 8 + 127) / 128 * 128);
+  const size_t slot = p.ring_fac + (size_t)fac_block_elems(sh.nvmax) * sizeof(double);
+  const size_t slot_al = (slot + 127) / 128 * 128;
+  p.staged = ((o + 127) / 128 * 128) + 2 * slot_al <= kMaxSmem;
+  if (p.staged) {
+    p.ring0 = take(slot_al, 128);
+    p.ring1 = take(slot_al, 128);
+  } else {
+    p.ring0 = p.ring1 = 0;
+  }
+  p.bytes = o;
+  return p;
 }
 
+namespace {
+
+constexpr double kIrFailRatio = 1e-6;      // mixed path: IR residual ratio that triggers FP64 factors
+
+using namespace dev;
+
 // ---------------------------------------------------------------------------
-// block-wide reductions (fixed order: the result depends only on blockDim)
+// block-wide reductions (max/min are exact, so their order does not matter)
 // ---------------------------------------------------------------------------
-struct OpSum {
-  __device__ double operator()(double a, double b) const { return a + b; }
-};
 struct OpMax {
   __device__ double operator()(double a, double b) const { return fmax(a, b); }
 };
@@ -74,18 +110,30 @@ __device__ double block_reduce(double v, double* red, Op op) {
 // ---------------------------------------------------------------------------
 // per-block context
 // ---------------------------------------------------------------------------
+struct Ring {
+  unsigned char* buf[2];
+  uint64_t* bar;     // two mbarriers
+  uint32_t parity;   // bit b: parity of the next phase of buffer b
+  uint32_t fac_off;  // byte offset of the factor block within a buffer
+  bool staged;       // false: read stages from global memory
+  bool ok;           // every copy landed
+};
+
 struct Ctx {
   const Batch* B;
   const StageDesc* st;  // shared-memory copy of this QP's stage table
   int N;
-  int nact;             // active (unmasked) sides
-  int nside;            // all sides of this QP
-  double* red;          // reduction scratch (32 doubles)
-  double* chunk;        // per-32-side partial sums for fixed_sum
-  double* vbuf;         // vector scratch (6 * vmax doubles)
+  int nact;       // active (unmasked) sides
+  int nside;      // all sides of this QP
+  int v0, v1;     // this QP's range in the stage-variable vectors
+  int e0, e1;     // ... in the dynamics vectors
+  double* red;    // reduction scratch (32 doubles)
+  double* chunk;  // per-32-side partial sums for fixed_sum
+  double* vbuf;   // vector scratch (8 * vmax doubles)
   int vmax;
-  void* mat;            // matrix scratch (Tf): L_{n+1}, Phi, M
-  int nvmax, nxmax, nemax;
+  void* mat;  // matrix scratch (Tf): L_{n+1}, Phi, M
+  int nvmax, nxmax;
+  Ring ring;
 };
 
 // Sum of f(i), i in [0, count), in an order fixed by `count` alone: 32-term
@@ -120,12 +168,21 @@ __device__ double fixed_sum(const Ctx& C, int count, F f) {
 __device__ __forceinline__ StageData lay(const StageDesc& s) {
   return stage_data_layout(s.nx, s.nu, s.nx1, s.nbu + s.nbx, s.ng);
 }
+__device__ __forceinline__ const int32_t* box_idx(const double* D, const StageData& L) {
+  return reinterpret_cast<const int32_t*>(D + L.box);
+}
+__device__ __forceinline__ int elim_size(const StageDesc& s, int n) { return n == 0 ? s.nx + s.nu : s.nu; }
 
-// value of constraint c of stage s at the stage vector y (global, length nv)
-__device__ __forceinline__ double cons_value(const Batch& B, const StageDesc& s, const StageData& L,
-                                             const double* D, int c, const double* y) {
+template <typename Tf>
+__device__ __forceinline__ Tf* fac_global(const Batch& B, const StageDesc& s) {
+  return static_cast<Tf*>(B.fac) + s.fac;
+}
+
+// value of constraint c of stage s at the stage vector y (length nv)
+__device__ __forceinline__ double cons_value(const StageDesc& s, const StageData& L, const double* D, int c,
+                                             const double* y) {
   const int nb = s.nbu + s.nbx;
-  if (c < nb) return y[B.idx[s.idx + c]];
+  if (c < nb) return y[box_idx(D, L)[c]];
   const int nv = s.nx + s.nu;
   const double* row = D + L.DC + (int64_t)(c - nb) * nv;
   double v = 0.0;
@@ -134,69 +191,109 @@ __device__ __forceinline__ double cons_value(const Batch& B, const StageDesc& s,
 }
 
 // ---------------------------------------------------------------------------
-// a1: residual function of eq. (delta).  With `lin` the constant terms
-// (r, q, b and bounds) are dropped and (add_g, add_b) are added instead:
-// that is the iterative-refinement residual of Sec. 3.4 for a direction.
+// stage sweeps over the bulk-copy ring
 // ---------------------------------------------------------------------------
-__device__ __noinline__ void residual_g_b(const Ctx& C, const double* y, const double* pi, const double* lam,
-                             double* og, double* ob, bool lin, const double* add_g,
-                             const double* add_b) {
+__device__ __forceinline__ void ring_issue(Ctx& C, int n, int b, int fac_elem) {
   const Batch& B = *C.B;
-  const int tid = threadIdx.x, NT = blockDim.x;
-  for (int n = 0; n <= C.N; ++n) {
-    const StageDesc s = C.st[n];
-    const StageData L = lay(s);
-    const double* D = B.data + s.data;
-    const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng;
-    const double* yn = y + s.var;
-    for (int i = tid; i < nv; i += NT) {
-      const double* row = D + L.RSQ + (int64_t)i * nv;
-      double acc = lin ? add_g[s.var + i] : D[L.rq + i];
-      for (int j = 0; j < nv; ++j) acc = fma(row[j], yn[j], acc);
-      if (n < C.N) {
-        const double* ba = D + L.BAt + (int64_t)i * s.nx1;
-        const double* pn1 = pi + s.eq;
-        for (int k = 0; k < s.nx1; ++k) acc = fma(ba[k], pn1[k], acc);
-      }
-      if (n > 0 && i >= s.nu) acc -= pi[C.st[n - 1].eq + (i - s.nu)];
-      const double* lm = lam + s.side;
-      for (int g = 0; g < s.ng; ++g) {
-        const double dc = D[L.DC + (int64_t)g * nv + i];
-        acc = fma(-dc, lm[nb + g] - lm[nc + nb + g], acc);
-      }
-      og[s.var + i] = acc;
-    }
-    if (n < C.N) {
-      const double* yn1 = y + C.st[n + 1].var + C.st[n + 1].nu;
-      for (int k = tid; k < s.nx1; k += NT) {
-        double acc = lin ? add_b[s.eq + k] : D[L.b + k];
-        for (int i = 0; i < nv; ++i) acc = fma(D[L.BAt + (int64_t)i * s.nx1 + k], yn[i], acc);
-        ob[s.eq + k] = acc - yn1[k];
-      }
-    }
+  const StageDesc& s = C.st[n];
+  if (threadIdx.x == 0) {
+    const uint32_t dbytes = (uint32_t)(lay(s).size * 8);
+    const uint32_t fbytes = fac_elem ? (uint32_t)(fac_block_elems(s.nx + s.nu) * fac_elem) : 0u;
+    fence_async_shared();
+    mbar_arrive_expect_tx(&C.ring.bar[b], dbytes + fbytes);
+    bulk_g2s(C.ring.buf[b], B.data + s.data, dbytes, &C.ring.bar[b]);
+    if (fbytes)
+      bulk_g2s(C.ring.buf[b] + C.ring.fac_off, static_cast<const unsigned char*>(B.fac) + s.fac * fac_elem, fbytes,
+               &C.ring.bar[b]);
   }
-  __syncthreads();
-  // box rows of -C' lambda (indices within a stage are distinct)
-  for (int n = 0; n <= C.N; ++n) {
-    const StageDesc s = C.st[n];
-    const int nb = s.nbu + s.nbx, nc = nb + s.ng;
-    const double* lm = lam + s.side;
-    for (int c = tid; c < nb; c += NT) og[s.var + B.idx[s.idx + c]] -= lm[c] - lm[nc + c];
-  }
-  __syncthreads();
 }
 
-// r_d = -C y + d + t per side; returns max |r_d| over active sides.
-__device__ __noinline__ double residual_d(const Ctx& C, const double* y, const double* t, double* rd) {
+__device__ __forceinline__ void ring_wait(Ctx& C, int b) {
+  // once a copy is lost the QP's results are void: stop waiting
+  const bool ok = C.ring.ok && mbar_wait(&C.ring.bar[b], (C.ring.parity >> b) & 1u);
+  C.ring.parity ^= 1u << b;
+  C.ring.ok = C.ring.ok && ok;
+}
+
+// Calls f(n, D, F) for every stage, forward or backward.  D is the stage data
+// block and F (when fac_elem > 0) the stage factor block, both in shared
+// memory when the ring is on.  f may synchronise internally; the sweep adds a
+// barrier after each stage before its buffer is refilled.
+template <class F>
+__device__ void sweep(Ctx& C, bool backward, int fac_elem, F f) {
   const Batch& B = *C.B;
-  double mx = 0.0;
-  for (int n = 0; n <= C.N; ++n) {
-    const StageDesc s = C.st[n];
-    const StageData L = lay(s);
-    const double* D = B.data + s.data;
-    const int nc = s.nbu + s.nbx + s.ng;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      const double v = cons_value(B, s, L, D, c, y + s.var);
+  const int N = C.N;
+  if (!C.ring.staged) {
+    for (int k = 0; k <= N; ++k) {
+      const int n = backward ? N - k : k;
+      const StageDesc& s = C.st[n];
+      const unsigned char* fac = static_cast<const unsigned char*>(B.fac) + s.fac * (fac_elem ? fac_elem : 1);
+      f(n, B.data + s.data, static_cast<const void*>(fac));
+      __syncthreads();
+    }
+    return;
+  }
+  ring_issue(C, backward ? N : 0, 0, fac_elem);
+  for (int k = 0; k <= N; ++k) {
+    const int n = backward ? N - k : k, b = k & 1;
+    if (k < N) ring_issue(C, backward ? n - 1 : n + 1, b ^ 1, fac_elem);
+    ring_wait(C, b);
+    f(n, reinterpret_cast<const double*>(C.ring.buf[b]), static_cast<const void*>(C.ring.buf[b] + C.ring.fac_off));
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a1: residual function of eq. (delta) for one stage.  With `lin` the constant
+// terms (r, q, b and bounds) are dropped and (add_g, add_b) are added instead:
+// that is the iterative-refinement residual of Sec. 3.4 for a direction.
+// Updates the running max of |r_g|, |r_b| (and |r_d| when rd != nullptr).
+// ---------------------------------------------------------------------------
+struct Max3 {
+  double g, b, d;
+};
+
+__device__ void stage_residual(const Ctx& C, int n, const double* D, const double* y, const double* pi,
+                               const double* lam, const double* t, double* og, double* ob, double* rd, bool lin,
+                               const double* add_g, const double* add_b, Max3& mx) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const StageDesc s = C.st[n];
+  const StageData L = lay(s);
+  const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng, nx1 = s.nx1;
+  const double* yn = y + s.var;
+  const double* lm = lam + s.side;
+  const int32_t* bmap = box_idx(D, L) + nb;
+  for (int i = tid; i < nv; i += NT) {
+    const double* row = D + L.RSQ + (int64_t)i * L.ldr;
+    double acc = lin ? add_g[s.var + i] : D[L.rq + i];
+    for (int j = 0; j < nv; ++j) acc = fma(row[j], yn[j], acc);
+    if (n < C.N) {
+      const double* ba = D + L.BAt + (int64_t)i * L.ldb;
+      const double* pn1 = pi + s.eq;
+      for (int k = 0; k < nx1; ++k) acc = fma(ba[k], pn1[k], acc);
+    }
+    if (n > 0 && i >= s.nu) acc -= pi[C.st[n - 1].eq + (i - s.nu)];
+    for (int g = 0; g < s.ng; ++g) acc = fma(-D[L.DC + (int64_t)g * nv + i], lm[nb + g] - lm[nc + nb + g], acc);
+    if (nb > 0) {
+      const int c = bmap[i];
+      if (c >= 0) acc -= lm[c] - lm[nc + c];
+    }
+    og[s.var + i] = acc;
+    mx.g = fmax(mx.g, fabs(acc));
+  }
+  if (n < C.N) {
+    const double* yn1 = y + C.st[n + 1].var + C.st[n + 1].nu;
+    for (int k = tid; k < nx1; k += NT) {
+      double acc = lin ? add_b[s.eq + k] : D[L.b + k];
+      for (int i = 0; i < nv; ++i) acc = fma(D[L.BAt + (int64_t)i * L.ldb + k], yn[i], acc);
+      acc -= yn1[k];
+      ob[s.eq + k] = acc;
+      mx.b = fmax(mx.b, fabs(acc));
+    }
+  }
+  if (rd != nullptr) {
+    for (int c = tid; c < nc; c += NT) {
+      const double v = cons_value(s, L, D, c, yn);
       const double lo = D[L.lo + c], hi = D[L.hi + c];
       const int il = s.side + c, iu = s.side + nc + c;
       double a = 0.0, b = 0.0;
@@ -204,213 +301,162 @@ __device__ __noinline__ double residual_d(const Ctx& C, const double* y, const d
       if (hi != INFINITY) b = v - hi + t[iu];
       rd[il] = a;
       rd[iu] = b;
-      mx = fmax(mx, fmax(fabs(a), fabs(b)));
+      mx.d = fmax(mx.d, fmax(fabs(a), fabs(b)));
     }
   }
-  return mx;
 }
 
 struct Norms {
   double g, b, d, mu;
 };
 
-__device__ __noinline__ Norms residuals(const Ctx& C) {
+__device__ Norms residuals(Ctx& C) {
   const Batch& B = *C.B;
-  residual_g_b(C, B.y, B.pi, B.lam, B.rg, B.rb, false, nullptr, nullptr);
-  double md = residual_d(C, B.y, B.t, B.rd);
-  double mg = 0.0, mb = 0.0;
-  const int q0v = C.st[0].var, q1v = C.st[C.N].var + C.st[C.N].nx + C.st[C.N].nu;
-  for (int i = q0v + threadIdx.x; i < q1v; i += blockDim.x) mg = fmax(mg, fabs(B.rg[i]));
-  const int q0e = C.st[0].eq, q1e = C.st[C.N].eq;
-  for (int i = q0e + threadIdx.x; i < q1e; i += blockDim.x) mb = fmax(mb, fabs(B.rb[i]));
+  Max3 mx{0.0, 0.0, 0.0};
+  sweep(C, false, 0, [&](int n, const double* D, const void*) {
+    stage_residual(C, n, D, B.y, B.pi, B.lam, B.t, B.rg, B.rb, B.rd, false, nullptr, nullptr, mx);
+  });
   // masked sides hold lambda = 0 and add nothing
   const int s0 = C.st[0].side;
   const double* lam = B.lam + s0;
   const double* tt = B.t + s0;
   const double sm = fixed_sum(C, C.nside, [&](int i) { return lam[i] * tt[i]; });
   Norms r;
-  r.g = block_reduce(mg, C.red, OpMax());
-  r.b = block_reduce(mb, C.red, OpMax());
-  r.d = block_reduce(md, C.red, OpMax());
+  r.g = block_reduce(mx.g, C.red, OpMax());
+  r.b = block_reduce(mx.b, C.red, OpMax());
+  r.d = block_reduce(mx.d, C.red, OpMax());
   r.mu = C.nact ? sm / C.nact : 0.0;
   return r;
 }
 
 // ---------------------------------------------------------------------------
-// a2: reduced gradient gt = r_g - C'(W r_d - T^{-1} r_m), W = Lambda T^{-1}
+// a3: square-root Riccati factorisation, one stage (called for n = N..0)
 // ---------------------------------------------------------------------------
-__device__ __noinline__ void reduced_rhs(const Ctx& C, const double* rg, const double* rd, const double* rm,
-                            double* gt) {
+template <typename Tf>
+__device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
   const Batch& B = *C.B;
   const int tid = threadIdx.x, NT = blockDim.x;
-  for (int n = 0; n <= C.N; ++n) {
-    const StageDesc s = C.st[n];
-    const StageData L = lay(s);
-    const double* D = B.data + s.data;
-    const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng;
-    const double* lm = B.lam + s.side;
-    const double* tt = B.t + s.side;
-    const double* d = rd + s.side;
-    const double* m = rm + s.side;
-    for (int i = tid; i < nv; i += NT) {
-      double acc = rg[s.var + i];
-      for (int g = 0; g < s.ng; ++g) {
-        const int l = nb + g, u = nc + nb + g;
-        double v = 0.0;
-        if (D[L.lo + l] != -INFINITY) v += (lm[l] * d[l] - m[l]) / tt[l];
-        if (D[L.hi + l] != INFINITY) v -= (lm[u] * d[u] - m[u]) / tt[u];
-        acc = fma(-D[L.DC + (int64_t)g * nv + i], v, acc);
-      }
-      gt[s.var + i] = acc;
-    }
-  }
-  __syncthreads();
-  for (int n = 0; n <= C.N; ++n) {
-    const StageDesc s = C.st[n];
-    const StageData L = lay(s);
-    const double* D = B.data + s.data;
-    const int nb = s.nbu + s.nbx, nc = nb + s.ng;
-    const double* lm = B.lam + s.side;
-    const double* tt = B.t + s.side;
-    const double* d = rd + s.side;
-    const double* m = rm + s.side;
-    for (int c = tid; c < nb; c += NT) {
-      double v = 0.0;
-      if (D[L.lo + c] != -INFINITY) v += (lm[c] * d[c] - m[c]) / tt[c];
-      if (D[L.hi + c] != INFINITY) v -= (lm[nc + c] * d[nc + c] - m[nc + c]) / tt[nc + c];
-      gt[s.var + B.idx[s.idx + c]] -= v;
-    }
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// a3: square-root Riccati factorisation, stages N..0
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int elim_size(const StageDesc& s, int n) { return n == 0 ? s.nx + s.nu : s.nu; }
-
-template <typename Tf>
-__device__ __forceinline__ Tf* fac_ptr(const Batch& B, const StageDesc& s) {
-  return static_cast<Tf*>(B.fac) + s.fac;
-}
-
-// Returns false when a pivot is not positive (not positive definite).
-template <typename Tf>
-__device__ __noinline__ bool factor(const Ctx& C, double reg) {
-  const Batch& B = *C.B;
-  const int tid = threadIdx.x, NT = blockDim.x;
-  Tf* sL = static_cast<Tf*>(C.mat);                      // L_{n+1}: nx1 x nx1
-  Tf* sPhi = sL + C.nxmax * C.nxmax;                      // nv x nv
-  Tf* sM = sPhi + C.nvmax * C.nvmax;                      // nv x nx1, also X temp
-  Tf* sw = reinterpret_cast<Tf*>(C.vbuf);                 // per-constraint weight
+  Tf* sL = static_cast<Tf*>(C.mat);        // L_{n+1}: nx1 x nx1
+  Tf* sPhi = sL + C.nxmax * C.nxmax;       // nv x nv
+  Tf* sM = sPhi + C.nvmax * C.nvmax;       // nv x nx1, also X temp
+  Tf* sw = reinterpret_cast<Tf*>(C.vbuf);  // per-constraint weight, then pivots
   bool ok = true;
-  for (int n = C.N; n >= 0; --n) {
-    const StageDesc s = C.st[n];
-    const StageData L = lay(s);
-    const double* D = B.data + s.data;
-    const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng, nx1 = s.nx1;
-    const int ne = elim_size(s, n), nk = nv - ne;
-    const double* lm = B.lam + s.side;
-    const double* tt = B.t + s.side;
-    // barrier weights W_lo + W_hi per constraint
-    for (int c = tid; c < nc; c += NT) {
-      double w = 0.0;
-      if (D[L.lo + c] != -INFINITY) w += lm[c] / tt[c];
-      if (D[L.hi + c] != INFINITY) w += lm[nc + c] / tt[nc + c];
-      sw[c] = (Tf)w;
+  const StageDesc s = C.st[n];
+  const StageData L = lay(s);
+  const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng, nx1 = s.nx1;
+  const int ne = elim_size(s, n), nk = nv - ne;
+  const double* lm = B.lam + s.side;
+  const double* tt = B.t + s.side;
+  const int32_t* bmap = box_idx(D, L) + nb;
+  // barrier weights W_lo + W_hi per constraint
+  for (int c = tid; c < nc; c += NT) {
+    double w = 0.0;
+    if (D[L.lo + c] != -INFINITY) w += lm[c] / tt[c];
+    if (D[L.hi + c] != INFINITY) w += lm[nc + c] / tt[nc + c];
+    sw[c] = (Tf)w;
+  }
+  // M = [B A]' L_{n+1}
+  if (n < C.N) {
+    for (int e = tid; e < nv * nx1; e += NT) {
+      const int i = e / nx1, j = e - i * nx1;
+      const double* ba = D + L.BAt + (int64_t)i * L.ldb;
+      Tf acc = 0;
+      for (int k = j; k < nx1; ++k) acc += (Tf)ba[k] * sL[k * nx1 + j];
+      sM[i * nx1 + j] = acc;
     }
-    // M = [B A]' L_{n+1}
-    if (n < C.N) {
-      for (int e = tid; e < nv * nx1; e += NT) {
-        const int i = e / nx1, j = e - i * nx1;
-        const double* ba = D + L.BAt + (int64_t)i * nx1;
-        Tf acc = 0;
-        for (int k = j; k < nx1; ++k) acc += (Tf)ba[k] * sL[k * nx1 + j];
-        sM[i * nx1 + j] = acc;
-      }
+  }
+  __syncthreads();
+  // Phi = RSQ + reg I + W_box + [D C]' diag(w_g) [D C] + M M'   (lower triangle)
+  for (int e = tid; e < nv * nv; e += NT) {
+    const int i = e / nv, j = e - i * nv;
+    if (j > i) continue;
+    Tf acc = (Tf)D[L.RSQ + (int64_t)i * L.ldr + j];
+    if (i == j) {
+      acc += (Tf)reg;
+      if (nb > 0 && bmap[i] >= 0) acc += sw[bmap[i]];
     }
-    __syncthreads();
-    // Phi = RSQ + reg I + [D C]' diag(w_g) [D C] + M M'   (lower triangle)
-    for (int e = tid; e < nv * nv; e += NT) {
-      const int i = e / nv, j = e - i * nv;
-      if (j > i) continue;
-      Tf acc = (Tf)D[L.RSQ + (int64_t)i * nv + j];
-      if (i == j) acc += (Tf)reg;
-      for (int g = 0; g < s.ng; ++g)
-        acc += (Tf)D[L.DC + (int64_t)g * nv + i] * sw[nb + g] * (Tf)D[L.DC + (int64_t)g * nv + j];
-      if (n < C.N)
-        for (int k = 0; k < nx1; ++k) acc += sM[i * nx1 + k] * sM[j * nx1 + k];
-      sPhi[i * nv + j] = acc;
+    for (int g = 0; g < s.ng; ++g)
+      acc += (Tf)D[L.DC + (int64_t)g * nv + i] * sw[nb + g] * (Tf)D[L.DC + (int64_t)g * nv + j];
+    if (n < C.N)
+      for (int k = 0; k < nx1; ++k) acc += sM[i * nx1 + k] * sM[j * nx1 + k];
+    sPhi[i * nv + j] = acc;
+  }
+  __syncthreads();
+  // right-looking Cholesky, outer-product form on the unscaled columns
+  for (int k = 0; k < nv; ++k) {
+    Tf d = sPhi[k * nv + k];
+    if (!(d > (Tf)0)) {
+      ok = false;
+      d = (Tf)1;
     }
-    __syncthreads();
-    for (int c = tid; c < nb; c += NT) {
-      const int k = B.idx[s.idx + c];
-      sPhi[k * nv + k] += sw[c];
-    }
-    __syncthreads();
-    // right-looking Cholesky, outer-product form on the unscaled columns
-    for (int k = 0; k < nv; ++k) {
-      Tf d = sPhi[k * nv + k];
-      if (!(d > (Tf)0)) {
-        ok = false;
-        d = (Tf)1;
-      }
-      const Tf inv = (Tf)1 / d;
-      for (int i = k + 1 + tid; i < nv; i += NT) {
-        const Tf lik = sPhi[i * nv + k] * inv;
-        Tf* ri = sPhi + i * nv;
-        for (int j = k + 1; j <= i; ++j) ri[j] -= lik * sPhi[j * nv + k];
-      }
-      __syncthreads();
-    }
-    // scale columns: L_jj = sqrt(d_j), L_ij = Phi_ij / sqrt(d_j)
-    Tf* sdiag = sw;  // weights no longer needed
-    for (int j = tid; j < nv; j += NT) {
-      Tf d = sPhi[j * nv + j];
-      sdiag[j] = d > (Tf)0 ? sqrt(d) : (Tf)1;
+    const Tf inv = (Tf)1 / d;
+    for (int i = k + 1 + tid; i < nv; i += NT) {
+      const Tf lik = sPhi[i * nv + k] * inv;
+      Tf* ri = sPhi + i * nv;
+      for (int j = k + 1; j <= i; ++j) ri[j] -= lik * sPhi[j * nv + k];
     }
     __syncthreads();
-    for (int e = tid; e < nv * nv; e += NT) {
-      const int i = e / nv, j = e - i * nv;
-      if (j > i) continue;
-      sPhi[i * nv + j] = (i == j) ? sdiag[j] : sPhi[i * nv + j] / sdiag[j];
+  }
+  // scale columns: L_jj = sqrt(d_j), L_ij = Phi_ij / sqrt(d_j)
+  Tf* sdiag = sw;  // weights no longer needed
+  for (int j = tid; j < nv; j += NT) {
+    const Tf d = sPhi[j * nv + j];
+    sdiag[j] = d > (Tf)0 ? sqrt(d) : (Tf)1;
+  }
+  __syncthreads();
+  for (int e = tid; e < nv * nv; e += NT) {
+    const int i = e / nv, j = e - i * nv;
+    if (j > i) continue;
+    sPhi[i * nv + j] = (i == j) ? sdiag[j] : sPhi[i * nv + j] / sdiag[j];
+  }
+  __syncthreads();
+  // X = L_ee^{-1} (lower), column j by thread j, into the M buffer
+  for (int j = tid; j < ne; j += NT) {
+    sM[j * ne + j] = (Tf)1 / sPhi[j * nv + j];
+    for (int i = j + 1; i < ne; ++i) {
+      Tf acc = 0;
+      for (int k = j; k < i; ++k) acc += sPhi[i * nv + k] * sM[k * ne + j];
+      sM[i * ne + j] = -acc / sPhi[i * nv + i];
     }
-    __syncthreads();
-    // X = L_ee^{-1} (lower), column j by thread j, into the M buffer
-    for (int j = tid; j < ne; j += NT) {
-      sM[j * ne + j] = (Tf)1 / sPhi[j * nv + j];
-      for (int i = j + 1; i < ne; ++i) {
-        Tf acc = 0;
-        for (int k = j; k < i; ++k) acc += sPhi[i * nv + k] * sM[k * ne + j];
-        sM[i * ne + j] = -acc / sPhi[i * nv + i];
-      }
-    }
-    __syncthreads();
-    for (int e = tid; e < ne * ne; e += NT) {
-      const int i = e / ne, j = e - i * ne;
-      if (j <= i) sPhi[i * nv + j] = sM[i * ne + j];
-    }
-    __syncthreads();
-    // store the factor, keep L_n = L_kk for stage n-1
-    Tf* F = fac_ptr<Tf>(B, s);
-    for (int e = tid; e < nv * nv; e += NT) {
-      const int i = e / nv, j = e - i * nv;
-      F[e] = (j <= i) ? sPhi[e] : (Tf)0;
-    }
-    for (int e = tid; e < nk * nk; e += NT) {
-      const int i = e / nk, j = e - i * nk;
-      sL[i * nk + j] = (j <= i) ? sPhi[(ne + i) * nv + ne + j] : (Tf)0;
-    }
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int e = tid; e < ne * ne; e += NT) {
+    const int i = e / ne, j = e - i * ne;
+    if (j <= i) sPhi[i * nv + j] = sM[i * ne + j];
+  }
+  __syncthreads();
+  // store the factor, keep L_n = L_kk for stage n-1
+  Tf* F = fac_global<Tf>(B, s);
+  for (int e = tid; e < nv * nv; e += NT) {
+    const int i = e / nv, j = e - i * nv;
+    F[e] = (j <= i) ? sPhi[e] : (Tf)0;
+  }
+  for (int e = tid; e < nk * nk; e += NT) {
+    const int i = e / nk, j = e - i * nk;
+    sL[i * nk + j] = (j <= i) ? sPhi[(ne + i) * nv + ne + j] : (Tf)0;
   }
   return ok;
 }
 
+template <typename Tf>
+__device__ bool factor(Ctx& C, double reg) {
+  bool ok = true;
+  sweep(C, true, 0, [&](int n, const double* D, const void*) { ok = factor_stage<Tf>(C, n, D, reg) && ok; });
+  // factor blocks were written through the generic proxy; the solves read them
+  // with bulk copies (async proxy)
+  fence_async_global();
+  __syncthreads();
+  return ok;
+}
+
 // ---------------------------------------------------------------------------
-// a4: Riccati solve of eq. (kkt) for right-hand side (gt, rb) -> (dy, dpi)
+// a2 + a4: Riccati solve of eq. (delta) for right-hand side (g, b) with the
+// reduced gradient gt = g - C'(W r_d - T^{-1} r_m) formed per stage
+// (rd = rm = nullptr: gt = g), -> (dy, dpi); then dt, dlam recovered in FP64.
 // ---------------------------------------------------------------------------
 template <typename Tf>
-__device__ __noinline__ void riccati_solve(const Ctx& C, const double* gt, const double* rb, double* dy, double* dpi) {
+__device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const double* rm, const double* rb,
+                                double* dy, double* dpi, double* dlam, double* dt) {
   const Batch& B = *C.B;
   const int tid = threadIdx.x, NT = blockDim.x;
   Tf* va = reinterpret_cast<Tf*>(C.vbuf);
@@ -418,43 +464,65 @@ __device__ __noinline__ void riccati_solve(const Ctx& C, const double* gt, const
   Tf* phi = vb + C.vmax;
   Tf* pn1 = phi + C.vmax;  // p_{n+1}
   Tf* ln = pn1 + C.vmax;
-  double* lp = B.lp;       // per stage: l (ne entries) then p_n (nk entries)
+  Tf* sL = static_cast<Tf*>(C.mat);  // L_{n+1}
+  double* vs = C.vbuf + 5 * C.vmax;  // per-constraint v_lo - v_hi, v = (lambda r_d - r_m) / t
+  double* lp = B.lp;                 // per stage: l (ne entries) then p_n (nk entries)
+  const int fe = (int)sizeof(Tf);
+  double scale = 0.0;                // ||(gt, r_b)||inf of the reduced system
   // backward sweep
-  for (int n = C.N; n >= 0; --n) {
+  sweep(C, true, fe, [&](int n, const double* D, const void* Fv) {
+    const Tf* F = static_cast<const Tf*>(Fv);
     const StageDesc s = C.st[n];
     const StageData L = lay(s);
-    const double* D = B.data + s.data;
-    const int nv = s.nx + s.nu, nx1 = s.nx1;
+    const int nv = s.nx + s.nu, nx1 = s.nx1, nb = s.nbu + s.nbx, nc = nb + s.ng;
     const int ne = elim_size(s, n), nk = nv - ne;
-    const Tf* F = fac_ptr<Tf>(B, s);
+    const int32_t* bmap = box_idx(D, L) + nb;
+    if (rd != nullptr) {
+      const double* lm = B.lam + s.side;
+      const double* tt = B.t + s.side;
+      for (int c = tid; c < nc; c += NT) {
+        const int il = s.side + c, iu = s.side + nc + c;
+        double v = 0.0;
+        if (D[L.lo + c] != -INFINITY) v += (lm[c] * rd[il] - rm[il]) / tt[c];
+        if (D[L.hi + c] != INFINITY) v -= (lm[nc + c] * rd[iu] - rm[iu]) / tt[nc + c];
+        vs[c] = v;
+      }
+    }
     if (n < C.N) {
-      const StageDesc s1 = C.st[n + 1];
-      const int nv1 = s1.nx + s1.nu, ne1 = s1.nu;
-      const Tf* F1 = fac_ptr<Tf>(B, s1) + ne1 * nv1 + ne1;  // L_{n+1}, row stride nv1
       // va = L_{n+1}' rb_n
       for (int k = tid; k < nx1; k += NT) {
         Tf acc = 0;
-        for (int j = k; j < nx1; ++j) acc += F1[j * nv1 + k] * (Tf)rb[s.eq + j];
+        for (int j = k; j < nx1; ++j) acc += sL[j * nx1 + k] * (Tf)rb[s.eq + j];
         va[k] = acc;
       }
-      __syncthreads();
+    }
+    __syncthreads();
+    if (n < C.N) {
       // vb = L_{n+1} va + p_{n+1}
       for (int k = tid; k < nx1; k += NT) {
         Tf acc = pn1[k];
-        for (int j = 0; j <= k; ++j) acc += F1[k * nv1 + j] * va[j];
+        for (int j = 0; j <= k; ++j) acc += sL[k * nx1 + j] * va[j];
         vb[k] = acc;
       }
-      __syncthreads();
     }
+    __syncthreads();
     // phi = gt_n + [B A]' vb
     for (int i = tid; i < nv; i += NT) {
-      Tf acc = (Tf)gt[s.var + i];
+      double gi = g[s.var + i];
+      if (rd != nullptr) {
+        for (int gg = 0; gg < s.ng; ++gg) gi = fma(-D[L.DC + (int64_t)gg * nv + i], vs[nb + gg], gi);
+        if (nb > 0 && bmap[i] >= 0) gi -= vs[bmap[i]];
+      }
+      scale = fmax(scale, fabs(gi));
+      Tf acc = (Tf)gi;
       if (n < C.N) {
-        const double* ba = D + L.BAt + (int64_t)i * nx1;
+        const double* ba = D + L.BAt + (int64_t)i * L.ldb;
         for (int k = 0; k < nx1; ++k) acc += (Tf)ba[k] * vb[k];
       }
       phi[i] = acc;
     }
+    if (n < C.N)
+      for (int k = tid; k < nx1; k += NT) scale = fmax(scale, fabs(rb[s.eq + k]));
     __syncthreads();
     // l = X phi_e
     for (int i = tid; i < ne; i += NT) {
@@ -464,24 +532,44 @@ __device__ __noinline__ void riccati_solve(const Ctx& C, const double* gt, const
       lp[s.var + i] = (double)acc;
     }
     __syncthreads();
-    // p_n = phi_k - L_ke l  -> becomes p_{n+1} of stage n-1
+    // p_n = phi_k - L_ke l  -> p_{n+1} of stage n-1; L_n = L_kk -> L_{n+1} of stage n-1
     for (int i = tid; i < nk; i += NT) {
       Tf acc = phi[ne + i];
       for (int j = 0; j < ne; ++j) acc -= F[(ne + i) * nv + j] * ln[j];
       pn1[i] = acc;
       lp[s.var + ne + i] = (double)acc;
     }
-    __syncthreads();
-  }
-  // forward sweep
-  for (int n = 0; n <= C.N; ++n) {
+    for (int e = tid; e < nk * nk; e += NT) {
+      const int i = e / nk, j = e - i * nk;
+      sL[i * nk + j] = F[(ne + i) * nv + ne + j];
+    }
+  });
+  // forward sweep: pi_n at the start of stage n (needs L_n), then y_n and
+  // x_{n+1}, then dt, dlam of stage n
+  sweep(C, false, fe, [&](int n, const double* D, const void* Fv) {
+    const Tf* F = static_cast<const Tf*>(Fv);
     const StageDesc s = C.st[n];
     const StageData L = lay(s);
-    const double* D = B.data + s.data;
-    const int nv = s.nx + s.nu, nx1 = s.nx1;
+    const int nv = s.nx + s.nu, nx1 = s.nx1, nb = s.nbu + s.nbx, nc = nb + s.ng;
     const int ne = elim_size(s, n), nk = nv - ne;
-    const Tf* F = fac_ptr<Tf>(B, s);
     double* yn = dy + s.var;
+    if (n > 0) {
+      // pi_n = L_n (L_n' x_n) + p_n,  L_n = L_kk of this stage
+      const double* xn = yn + ne;
+      for (int k = tid; k < nk; k += NT) {
+        Tf acc = 0;
+        for (int j = k; j < nk; ++j) acc += F[(ne + j) * nv + ne + k] * (Tf)xn[j];
+        va[k] = acc;
+      }
+      __syncthreads();
+      const int eqp = C.st[n - 1].eq;
+      for (int k = tid; k < nk; k += NT) {
+        Tf acc = (Tf)lp[s.var + ne + k];
+        for (int j = 0; j <= k; ++j) acc += F[(ne + k) * nv + ne + j] * va[j];
+        dpi[eqp + k] = (double)acc;
+      }
+      __syncthreads();
+    }
     // va = l + L_ke' x_n
     for (int j = tid; j < ne; j += NT) {
       Tf acc = (Tf)lp[s.var + j];
@@ -497,74 +585,46 @@ __device__ __noinline__ void riccati_solve(const Ctx& C, const double* gt, const
     }
     __syncthreads();
     if (n < C.N) {
-      const StageDesc s1 = C.st[n + 1];
-      const int nv1 = s1.nx + s1.nu, ne1 = s1.nu;
-      const Tf* F1 = fac_ptr<Tf>(B, s1) + ne1 * nv1 + ne1;
-      double* x1 = dy + s1.var + s1.nu;
       // x_{n+1} = [B A] y_n + rb_n
+      double* x1 = dy + C.st[n + 1].var + C.st[n + 1].nu;
       for (int k = tid; k < nx1; k += NT) {
         Tf acc = (Tf)rb[s.eq + k];
-        for (int i = 0; i < nv; ++i) acc += (Tf)D[L.BAt + (int64_t)i * nx1 + k] * (Tf)yn[i];
+        for (int i = 0; i < nv; ++i) acc += (Tf)D[L.BAt + (int64_t)i * L.ldb + k] * (Tf)yn[i];
         x1[k] = (double)acc;
-        vb[k] = acc;
       }
-      __syncthreads();
-      // pi_{n+1} = L_{n+1}(L_{n+1}' x_{n+1}) + p_{n+1}
-      for (int k = tid; k < nx1; k += NT) {
-        Tf acc = 0;
-        for (int j = k; j < nx1; ++j) acc += F1[j * nv1 + k] * vb[j];
-        va[k] = acc;
-      }
-      __syncthreads();
-      for (int k = tid; k < nx1; k += NT) {
-        Tf acc = (Tf)lp[s1.var + ne1 + k];
-        for (int j = 0; j <= k; ++j) acc += F1[k * nv1 + j] * va[j];
-        dpi[s.eq + k] = (double)acc;
-      }
-      __syncthreads();
     }
-  }
-}
-
-// dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt) on active sides (0 elsewhere)
-__device__ __noinline__ void recover(const Ctx& C, const double* dy, double* dlam, double* dt) {
-  const Batch& B = *C.B;
-  for (int n = 0; n <= C.N; ++n) {
-    const StageDesc s = C.st[n];
-    const StageData L = lay(s);
-    const double* D = B.data + s.data;
-    const int nc = s.nbu + s.nbx + s.ng;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      const double v = cons_value(B, s, L, D, c, dy + s.var);
+    // dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt) on active sides
+    for (int c = tid; c < nc; c += NT) {
+      const double v = cons_value(s, L, D, c, yn);
       const int il = s.side + c, iu = s.side + nc + c;
+      const double dl = rd ? rd[il] : 0.0, du = rd ? rd[iu] : 0.0;
+      const double ml = rm ? rm[il] : 0.0, mu = rm ? rm[iu] : 0.0;
       if (D[L.lo + c] != -INFINITY) {
-        const double a = v - B.rd[il];
+        const double a = v - dl;
         dt[il] = a;
-        dlam[il] = -(B.rm[il] + B.lam[il] * a) / B.t[il];
+        dlam[il] = -(ml + B.lam[il] * a) / B.t[il];
       } else {
         dt[il] = 0.0;
         dlam[il] = 0.0;
       }
       if (D[L.hi + c] != INFINITY) {
-        const double a = -v - B.rd[iu];
+        const double a = -v - du;
         dt[iu] = a;
-        dlam[iu] = -(B.rm[iu] + B.lam[iu] * a) / B.t[iu];
+        dlam[iu] = -(mu + B.lam[iu] * a) / B.t[iu];
       } else {
         dt[iu] = 0.0;
         dlam[iu] = 0.0;
       }
     }
-  }
-  __syncthreads();
+  });
+  return block_reduce(scale, C.red, OpMax());
 }
 
 // elementwise pass over this QP's sides
 template <class F>
 __device__ void for_sides(const Ctx& C, F f) {
   const int s0 = C.st[0].side;
-  const StageDesc& last = C.st[C.N];
-  const int s1 = last.side + 2 * (last.nbu + last.nbx + last.ng);
-  for (int i = s0 + threadIdx.x; i < s1; i += blockDim.x) f(i);
+  for (int i = s0 + threadIdx.x; i < s0 + C.nside; i += blockDim.x) f(i);
 }
 
 // a5: largest alpha with lambda + alpha dlam >= 0 and t + alpha dt >= 0
@@ -599,56 +659,41 @@ struct Count {
   int ir = 0, fact = 0, fact64 = 0, solve = 0, res = 0;
 };
 
-// factor-precision solve of eq. (delta) for the current r_m, then FP64
-// recovery of (dlam, dt); with ir > 0, iterative refinement (Sec. 3.4).
+// Newton direction of eq. (delta) for the current r_m with the factors in
+// place; with ir > 0, iterative refinement on eq. (itref) (Sec. 3.4).
 // Returns the final refinement residual ratio (0 without refinement).
 template <typename Tf>
-__device__ __noinline__ double newton_dir(const Ctx& C, const Dir& d, int ir, double ir_tol, Count* cnt) {
+__device__ double newton_dir(Ctx& C, const Dir& d, int ir, double ir_tol, Count* cnt) {
   const Batch& B = *C.B;
-  reduced_rhs(C, B.rg, B.rd, B.rm, B.gt);
-  riccati_solve<Tf>(C, B.gt, B.rb, d.dy, d.dpi);
+  // mr: scale of the reduced right-hand side ||(gt, r_b)||inf
+  const double mr = riccati_solve<Tf>(C, B.rg, B.rd, B.rm, B.rb, d.dy, d.dpi, d.dlam, d.dt);
   ++cnt->solve;
-  recover(C, d.dy, d.dlam, d.dt);
   if (ir <= 0) return 0.0;
-  // ||rhs||inf of the reduced system
-  double mr = 0.0;
-  {
-    const int v0 = C.st[0].var, v1 = C.st[C.N].var + C.st[C.N].nx + C.st[C.N].nu;
-    for (int i = v0 + threadIdx.x; i < v1; i += blockDim.x) mr = fmax(mr, fabs(B.gt[i]));
-    const int e0 = C.st[0].eq, e1 = C.st[C.N].eq;
-    for (int i = e0 + threadIdx.x; i < e1; i += blockDim.x) mr = fmax(mr, fabs(B.rb[i]));
-  }
-  mr = block_reduce(mr, C.red, OpMax());
   double ratio = 0.0;
   for (int k = 0; k <= ir; ++k) {
     // residual of eq. (delta) for the direction (the r_d and r_m rows vanish
     // because dt and dlam are recovered from dy in FP64)
-    residual_g_b(C, d.dy, d.dpi, d.dlam, B.rg2, B.rb2, true, B.rg, B.rb);
+    Max3 mx{0.0, 0.0, 0.0};
+    sweep(C, false, 0, [&](int n, const double* D, const void*) {
+      stage_residual(C, n, D, d.dy, d.dpi, d.dlam, nullptr, B.rg2, B.rb2, nullptr, true, B.rg, B.rb, mx);
+    });
     ++cnt->res;
-    double m = 0.0;
-    const int v0 = C.st[0].var, v1 = C.st[C.N].var + C.st[C.N].nx + C.st[C.N].nu;
-    for (int i = v0 + threadIdx.x; i < v1; i += blockDim.x) m = fmax(m, fabs(B.rg2[i]));
-    const int e0 = C.st[0].eq, e1 = C.st[C.N].eq;
-    for (int i = e0 + threadIdx.x; i < e1; i += blockDim.x) m = fmax(m, fabs(B.rb2[i]));
-    m = block_reduce(m, C.red, OpMax());
+    const double m = block_reduce(fmax(mx.g, mx.b), C.red, OpMax());
     ratio = mr > 0.0 ? m / mr : 0.0;
     if (k == ir || m <= ir_tol * mr) break;
     // correction: same factors, the refinement residual as right-hand side
-    // (reduced gradient = r_g^ir since the r_d and r_m rows are zero)
-    riccati_solve<Tf>(C, B.rg2, B.rb2, B.dy2, B.dpi2);
-    for (int i = v0 + threadIdx.x; i < v1; i += blockDim.x) d.dy[i] += B.dy2[i];
-    for (int i = e0 + threadIdx.x; i < e1; i += blockDim.x) d.dpi[i] += B.dpi2[i];
+    riccati_solve<Tf>(C, B.rg2, nullptr, nullptr, B.rb2, B.dy2, B.dpi2, B.dlam2, B.dt2);
+    for (int i = C.v0 + threadIdx.x; i < C.v1; i += blockDim.x) d.dy[i] += B.dy2[i];
+    for (int i = C.e0 + threadIdx.x; i < C.e1; i += blockDim.x) d.dpi[i] += B.dpi2[i];
+    for_sides(C, [&](int i) {
+      d.dlam[i] += B.dlam2[i];
+      d.dt[i] += B.dt2[i];
+    });
     __syncthreads();
-    recover(C, d.dy, d.dlam, d.dt);
     ++cnt->ir;
     ++cnt->solve;
   }
   return ratio;
-}
-
-template <typename Tf>
-__device__ bool factor_dispatch(const Ctx& C, double reg) {
-  return factor<Tf>(C, reg);
 }
 
 // ---------------------------------------------------------------------------
@@ -656,24 +701,26 @@ __device__ bool factor_dispatch(const Ctx& C, double reg) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch B, const Shape sh,
                                                   const __grid_constant__ gq_ipm_arg arg, int kind,
-                                                  double sigma_mu, const DirOut out) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int q = B.order[blockIdx.x];
+                                                  double sigma_mu, const DirOut out, const int32_t* order) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int q = order[blockIdx.x];
   const QpDesc qd = B.qp[q];
   const int tid = threadIdx.x;
-  // shared-memory plan
-  StageDesc* sst = reinterpret_cast<StageDesc*>(smem);
-  size_t off = ((size_t)sh.nst_max * sizeof(StageDesc) + 15) & ~size_t(15);
-  double* red = reinterpret_cast<double*>(smem + off);
-  off += 32 * sizeof(double);
-  double* chunk = reinterpret_cast<double*>(smem + off);
-  off += (size_t)((sh.nside_max + 31) / 32 + 1) * sizeof(double);
-  const int vmax = B.nvmax + B.ngmax + 2;
-  double* vbuf = reinterpret_cast<double*>(smem + off);
-  off += (size_t)6 * vmax * sizeof(double);
-  void* mat = smem + off;
+  const SmemPlan P = smem_plan(B, sh);
+  StageDesc* sst = reinterpret_cast<StageDesc*>(smem + P.stages);
+  double* red = reinterpret_cast<double*>(smem + P.red);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P.bars);
+  int& s_count = *reinterpret_cast<int*>(smem + P.bars + 2 * sizeof(uint64_t));
 
   for (int n = tid; n <= qd.N; n += blockDim.x) sst[n] = B.st[qd.stage0 + n];
+  if (tid == 0) {
+    s_count = 0;
+    if (P.staged) {
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      fence_async_shared();
+    }
+  }
   __syncthreads();
 
   Ctx C;
@@ -681,27 +728,38 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
   C.st = sst;
   C.N = qd.N;
   C.red = red;
-  C.chunk = chunk;
+  C.chunk = reinterpret_cast<double*>(smem + P.chunk);
   C.nside = qd.nsidet;
-  C.vbuf = vbuf;
-  C.vmax = vmax;
-  C.mat = mat;
-  C.nvmax = B.nvmax;
-  C.nxmax = B.nxmax;
-  C.nemax = sh.ne_max;
+  C.v0 = qd.var0;
+  C.v1 = qd.var0 + qd.nvt;
+  C.e0 = qd.eq0;
+  C.e1 = qd.eq0 + qd.neqt;
+  C.vbuf = reinterpret_cast<double*>(smem + P.vec);
+  C.vmax = P.vmax;
+  C.mat = smem + P.mat;
+  C.nvmax = sh.nvmax;
+  C.nxmax = sh.nxmax;
+  C.ring.buf[0] = smem + P.ring0;
+  C.ring.buf[1] = smem + P.ring1;
+  C.ring.bar = bars;
+  C.ring.parity = 0;
+  C.ring.fac_off = (uint32_t)P.ring_fac;
+  C.ring.staged = P.staged;
+  C.ring.ok = true;
 
-  // count active sides
+  // count active sides (integer count: exact in any order)
   {
-    double cnt = 0.0;
-    for (int n = 0; n <= C.N; ++n) {
+    int cnt = 0;
+    sweep(C, false, 0, [&](int n, const double* D, const void*) {
       const StageDesc s = sst[n];
       const StageData L = lay(s);
-      const double* D = B.data + s.data;
       const int nc = s.nbu + s.nbx + s.ng;
-      for (int c = tid; c < nc; c += blockDim.x)
-        cnt += (D[L.lo + c] != -INFINITY) + (D[L.hi + c] != INFINITY);
-    }
-    C.nact = (int)block_reduce(cnt, red, OpSum());
+      for (int c = tid; c < nc; c += blockDim.x) cnt += (D[L.lo + c] != -INFINITY) + (D[L.hi + c] != INFINITY);
+    });
+    atomicAdd(&s_count, cnt);
+    __syncthreads();
+    C.nact = s_count;
+    __syncthreads();
   }
 
   const bool mixed = arg.precision == GQ_PREC_MIXED;
@@ -714,6 +772,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
       stats->res[1] = r.b;
       stats->res[2] = r.d;
       stats->res[3] = r.mu;
+      if (!C.ring.ok) stats->status = GQ_STATUS_TIMEOUT;
     }
     return;
   }
@@ -730,7 +789,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
     else
       newton_dir<double>(C, d, arg.ir_steps, arg.ir_tol, &cnt);
     if (tid == 0) {
-      stats->status = ok ? GQ_STATUS_CONVERGED : GQ_STATUS_NAN;
+      stats->status = !C.ring.ok ? GQ_STATUS_TIMEOUT : (ok ? GQ_STATUS_CONVERGED : GQ_STATUS_NAN);
       stats->ir_total = cnt.ir;
     }
     return;
@@ -742,17 +801,16 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
   {
     const bool warm1 = arg.warm_start >= 1, warm2 = arg.warm_start >= 2;
     if (!warm1) {
-      for (int i = qd.var0 + tid; i < qd.var0 + qd.nvt; i += blockDim.x) B.y[i] = 0.0;
-      for (int i = qd.eq0 + tid; i < qd.eq0 + qd.neqt; i += blockDim.x) B.pi[i] = 0.0;
+      for (int i = C.v0 + tid; i < C.v1; i += blockDim.x) B.y[i] = 0.0;
+      for (int i = C.e0 + tid; i < C.e1; i += blockDim.x) B.pi[i] = 0.0;
     }
     __syncthreads();
-    for (int n = 0; n <= C.N; ++n) {
+    sweep(C, false, 0, [&](int n, const double* D, const void*) {
       const StageDesc s = sst[n];
       const StageData L = lay(s);
-      const double* D = B.data + s.data;
       const int nc = s.nbu + s.nbx + s.ng;
       for (int c = tid; c < nc; c += blockDim.x) {
-        const double v = cons_value(B, s, L, D, c, B.y + s.var);
+        const double v = cons_value(s, L, D, c, B.y + s.var);
         const double lo = D[L.lo + c], hi = D[L.hi + c];
         const int il = s.side + c, iu = s.side + nc + c;
         if (lo != -INFINITY) {
@@ -780,8 +838,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
           B.t[iu] = 1.0;
         }
       }
-    }
-    __syncthreads();
+    });
   }
 
   int status = GQ_STATUS_MAX_ITER, it = 0, flags = 0;
@@ -793,6 +850,10 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
   while (true) {
     r = residuals(C);
     ++cnt.res;
+    if (!C.ring.ok) {
+      status = GQ_STATUS_TIMEOUT;
+      break;
+    }
     if (!(isfinite(r.g) && isfinite(r.b) && isfinite(r.d) && isfinite(r.mu))) {
       status = GQ_STATUS_NAN;
       break;
@@ -811,7 +872,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
     }
     if (arg.timeout_ns > 0) {
       int64_t el = globaltimer() - t_start;
-      // one thread's clock decides for the block
+      // one clock for the block
       el = (int64_t)block_reduce((double)el, red, OpMax());
       if (el > arg.timeout_ns) {
         status = GQ_STATUS_TIMEOUT;
@@ -873,8 +934,8 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
     } else {
       if (ir > 0) {
         // no inequalities: refine the single Newton step
-        double ratio = fp64 ? newton_dir<double>(C, d, ir, arg.ir_tol, &cnt)
-                            : newton_dir<float>(C, d, ir, arg.ir_tol, &cnt);
+        const double ratio = fp64 ? newton_dir<double>(C, d, ir, arg.ir_tol, &cnt)
+                                  : newton_dir<float>(C, d, ir, arg.ir_tol, &cnt);
         if (!fp64 && arg.fp64_fallback && !(ratio <= kIrFailRatio)) {
           fp64 = true;
           flags |= GQ_FLAG_FP64_FALLBACK;
@@ -884,8 +945,8 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
       alpha = 1.0;
     }
     // a8: step and clamp
-    for (int i = qd.var0 + tid; i < qd.var0 + qd.nvt; i += blockDim.x) B.y[i] += alpha * d.dy[i];
-    for (int i = qd.eq0 + tid; i < qd.eq0 + qd.neqt; i += blockDim.x) B.pi[i] += alpha * d.dpi[i];
+    for (int i = C.v0 + tid; i < C.v1; i += blockDim.x) B.y[i] += alpha * d.dy[i];
+    for (int i = C.e0 + tid; i < C.e1; i += blockDim.x) B.pi[i] += alpha * d.dpi[i];
     for_sides(C, [&](int i) {
       if (B.lam[i] != 0.0 || d.dlam[i] != 0.0) {
         B.lam[i] = fmax(B.lam[i] + alpha * d.dlam[i], arg.lam_min);
@@ -913,32 +974,26 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
 
 }  // namespace
 
-size_t ipm_smem_bytes(const Batch& b, const Shape& sh) {
-  const int vmax = b.nvmax + b.ngmax + 2;
-  size_t smem = ((size_t)sh.nst_max * sizeof(StageDesc) + 15) & ~size_t(15);
-  smem += 32 * sizeof(double) + (size_t)6 * vmax * sizeof(double);
-  smem += (size_t)((sh.nside_max + 31) / 32 + 1) * sizeof(double);
-  const int wide = b.nxmax > sh.ne_max ? b.nxmax : sh.ne_max;
-  const size_t mbuf = (size_t)b.nvmax * (wide > 0 ? wide : 1);
-  smem += ((size_t)b.nxmax * b.nxmax + (size_t)b.nvmax * b.nvmax + mbuf) * sizeof(double);
-  return smem;
-}
+size_t ipm_smem_bytes(const Batch& b, const Shape& sh) { return smem_plan(b, sh).bytes; }
 
 cudaError_t launch_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
-                       LaunchKind kind, double sigma_mu, const DirOut* out) {
+                       LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count) {
+  if (count <= 0) return cudaSuccess;
   const size_t smem = ipm_smem_bytes(b, sh);
   if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(ipm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+  // opt in to the dynamic shared memory this launch needs (per process; the
+  // attribute only ever grows)
+  static size_t attr_bytes = 48 * 1024;
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(ipm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_bytes = smem;
   }
-  int nt = ((b.nvmax + 31) / 32) * 32;
+  int nt = ((sh.nvmax + 31) / 32) * 32;
   nt = nt < 32 ? 32 : (nt > 256 ? 256 : nt);
   DirOut o{};
   if (out) o = *out;
-  ipm_kernel<<<b.nqp, nt, smem, stream>>>(b, sh, arg, (int)kind, sigma_mu, o);
+  ipm_kernel<<<count, nt, smem, stream>>>(b, sh, arg, (int)kind, sigma_mu, o, order);
   return cudaGetLastError();
 }
 

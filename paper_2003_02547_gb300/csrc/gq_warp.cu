@@ -1,0 +1,962 @@
+// Warp-per-QP IPM kernel for QPs whose stages all have nu + nx <= 32 and
+// nx <= 32 (the small stages of model predictive control).
+//
+// The algorithm is the one of gq_ipm.cu (Mehrotra predictor-corrector of
+// Sec. 4.2, square-root Riccati factorisation of eq. (kkt), Sec. 3.3, with
+// iterative refinement, Sec. 3.4), mapped onto one warp:
+//   * lane i owns row i of the stage matrices: the Riccati stage matrix Phi,
+//     the products M = [B A]' L_{n+1}, and element i of every stage vector;
+//   * the Cholesky factorisation runs on register rows, with the pivot and
+//     the factor column broadcast by warp shuffles -- no shared-memory
+//     read-modify-write chains and no block barriers;
+//   * shared-memory matrices use an odd row stride (33), so lane-per-row
+//     reads are free of bank conflicts;
+//   * each stage's data block (and in the solves its factor block) arrives
+//     by one 1-D bulk copy into a two-slot ring, one stage ahead;
+//   * the mixed-precision path reads an FP32 mirror of the data for the
+//     factorisation and solves (no FP64->FP32 conversions in inner loops),
+//     the FP64 data for residuals and refinement.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gq_device.h"
+#include "gq_internal.h"
+#include "gq_launch.h"
+
+namespace gq {
+namespace {
+
+using namespace dev;
+
+constexpr int LDS = 33;                 // shared-memory row stride
+constexpr double kIrFailRatio = 1e-6;   // mixed path: IR residual ratio that triggers FP64 factors
+
+__device__ __forceinline__ StageData wlay(const StageDesc& s) {
+  return stage_data_layout(s.nx, s.nu, s.nx1, s.nbu + s.nbx, s.ng);
+}
+__device__ __forceinline__ int welim(const StageDesc& s, int n) { return n == 0 ? s.nx + s.nu : s.nu; }
+
+template <typename T>
+__device__ __forceinline__ T wrsqrt(T x);
+template <>
+__device__ __forceinline__ float wrsqrt<float>(float x) {
+  return rsqrtf(x);
+}
+template <>
+__device__ __forceinline__ double wrsqrt<double>(double x) {
+  return rsqrt(x);
+}
+
+struct WCtx {
+  const Batch* B;
+  const StageDesc* st;
+  int N, nact, nside, side0, v0, v1, e0, e1, lane;
+  unsigned char* ring[2];
+  uint64_t* bar;
+  uint32_t parity;
+  uint32_t fac_off;
+  bool ok;
+  void* sL;    // L_{n+1}, 32 x LDS
+  void* sM;    // M, then X = L_ee^{-1}, 32 x LDS
+  void* sP;    // Phi and its factor, 32 x LDS
+  double* sv;  // per-constraint scratch (vmax doubles)
+  int vmax;
+};
+
+// deterministic sum over this QP's sides: 32-side chunks by butterfly, chunk
+// sums in order (every lane holds the same bits)
+template <class F>
+__device__ __forceinline__ double side_sum(const WCtx& C, F f) {
+  double acc = 0.0;
+  for (int c0 = 0; c0 < C.nside; c0 += 32) {
+    const int k = c0 + C.lane;
+    acc += warp_sum(k < C.nside ? f(C.side0 + k) : 0.0);
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// stage sweep over the bulk-copy ring
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void wissue(WCtx& C, int n, int b, const unsigned char* dbase, int delem,
+                                       const unsigned char* fbase, int felem) {
+  const StageDesc& s = C.st[n];
+  if (C.lane == 0) {
+    const uint32_t dbytes = (uint32_t)(wlay(s).size * delem);
+    const uint32_t fbytes = felem ? (uint32_t)(fac_block_elems(s.nx + s.nu) * felem) : 0u;
+    fence_async_shared();
+    mbar_arrive_expect_tx(&C.bar[b], dbytes + fbytes);
+    bulk_g2s(C.ring[b], dbase + s.data * delem, dbytes, &C.bar[b]);
+    if (fbytes) bulk_g2s(C.ring[b] + C.fac_off, fbase + s.fac * felem, fbytes, &C.bar[b]);
+  }
+}
+
+// f(n, data block, factor block) for every stage, forward or backward
+template <class F>
+__device__ void wsweep(WCtx& C, bool backward, const void* dbase, int delem, const void* fbase, int felem, F f) {
+  const unsigned char* db = static_cast<const unsigned char*>(dbase);
+  const unsigned char* fb = static_cast<const unsigned char*>(fbase);
+  const int N = C.N;
+  wissue(C, backward ? N : 0, 0, db, delem, fb, felem);
+  for (int k = 0; k <= N; ++k) {
+    const int n = backward ? N - k : k, b = k & 1;
+    if (k < N) wissue(C, backward ? n - 1 : n + 1, b ^ 1, db, delem, fb, felem);
+    // once a copy is lost the QP's results are void: stop waiting
+    const bool ok = C.ok && mbar_wait(&C.bar[b], (C.parity >> b) & 1u);
+    C.parity ^= 1u << b;
+    C.ok = C.ok && ok;
+    f(n, static_cast<const void*>(C.ring[b]), static_cast<const void*>(C.ring[b] + C.fac_off));
+    __syncwarp();
+  }
+}
+
+// value of general constraint g (row of [D C]) at the stage vector held one
+// element per lane
+template <typename T>
+__device__ __forceinline__ double gen_value(const WCtx& C, const T* D, const StageData& L, int nv, int g,
+                                            double yl) {
+  const double part = C.lane < nv ? (double)D[L.DC + (int64_t)g * nv + C.lane] * yl : 0.0;
+  return warp_sum(part);
+}
+
+// ---------------------------------------------------------------------------
+// a1: residuals of eq. (delta) for one stage, FP64 (lin: refinement residual)
+// ---------------------------------------------------------------------------
+struct WMax {
+  double g, b, d;
+};
+
+__device__ __noinline__ void wres_stage(WCtx& C, int n, const double* D, const double* y, const double* pi, const double* lam,
+                           const double* t, double* og, double* ob, double* rd, bool lin, const double* add_g,
+                           const double* add_b, WMax& mx) {
+  const Batch& B = *C.B;
+  const int lane = C.lane;
+  const StageDesc s = C.st[n];
+  const StageData L = wlay(s);
+  const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng, nx1 = s.nx1;
+  const int32_t* bidx = reinterpret_cast<const int32_t*>(D + L.box);
+  const int32_t* bmap = bidx + nb;
+  const double yl = lane < nv ? y[s.var + lane] : 0.0;
+  const double pl = (n < C.N && lane < nx1) ? pi[s.eq + lane] : 0.0;
+  const double* lm = lam + s.side;
+  // r_g, row `lane`
+  {
+    const double* row = D + L.RSQ + (int64_t)(lane < nv ? lane : 0) * L.ldr;
+    double a0 = 0.0, a1 = 0.0;
+    int j = 0;
+    for (; j + 1 < nv; j += 2) {
+      const double y0 = __shfl_sync(kFull, yl, j), y1 = __shfl_sync(kFull, yl, j + 1);
+      a0 = fma(row[j], y0, a0);
+      a1 = fma(row[j + 1], y1, a1);
+    }
+    if (j < nv) a0 = fma(row[j], __shfl_sync(kFull, yl, j), a0);
+    if (n < C.N) {
+      const double* ba = D + L.BAt + (int64_t)(lane < nv ? lane : 0) * L.ldb;
+      int k = 0;
+      for (; k + 1 < nx1; k += 2) {
+        const double p0 = __shfl_sync(kFull, pl, k), p1 = __shfl_sync(kFull, pl, k + 1);
+        a0 = fma(ba[k], p0, a0);
+        a1 = fma(ba[k + 1], p1, a1);
+      }
+      if (k < nx1) a0 = fma(ba[k], __shfl_sync(kFull, pl, k), a0);
+    }
+    if (lane < nv) {
+      double acc = (lin ? add_g[s.var + lane] : D[L.rq + lane]) + (a0 + a1);
+      if (n > 0 && lane >= s.nu) acc -= pi[C.st[n - 1].eq + (lane - s.nu)];
+      for (int g = 0; g < s.ng; ++g) acc = fma(-D[L.DC + (int64_t)g * nv + lane], lm[nb + g] - lm[nc + nb + g], acc);
+      if (nb > 0) {
+        const int c = bmap[lane];
+        if (c >= 0) acc -= lm[c] - lm[nc + c];
+      }
+      og[s.var + lane] = acc;
+      mx.g = fmax(mx.g, fabs(acc));
+    }
+  }
+  // r_b, row `lane`
+  if (n < C.N) {
+    double a0 = 0.0, a1 = 0.0;
+    const int kk = lane < nx1 ? lane : 0;
+    int i = 0;
+    for (; i + 1 < nv; i += 2) {
+      const double y0 = __shfl_sync(kFull, yl, i), y1 = __shfl_sync(kFull, yl, i + 1);
+      a0 = fma(D[L.BAt + (int64_t)i * L.ldb + kk], y0, a0);
+      a1 = fma(D[L.BAt + (int64_t)(i + 1) * L.ldb + kk], y1, a1);
+    }
+    if (i < nv) a0 = fma(D[L.BAt + (int64_t)i * L.ldb + kk], __shfl_sync(kFull, yl, i), a0);
+    if (lane < nx1) {
+      const double x1 = y[C.st[n + 1].var + C.st[n + 1].nu + lane];
+      const double acc = (lin ? add_b[s.eq + lane] : D[L.b + lane]) + (a0 + a1) - x1;
+      ob[s.eq + lane] = acc;
+      mx.b = fmax(mx.b, fabs(acc));
+    }
+  }
+  // r_d per side
+  if (rd != nullptr) {
+    for (int g = 0; g < s.ng; ++g) {
+      const double v = gen_value<double>(C, D, L, nv, g, yl);
+      if (lane == 0) C.sv[g] = v;
+    }
+    __syncwarp();
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+      const int c = c0 + lane;
+      const int src = (c < nb) ? bidx[c] : 0;
+      const double yb = __shfl_sync(kFull, yl, src);
+      if (c < nc) {
+        const double v = c < nb ? yb : C.sv[c - nb];
+        const double lo = D[L.lo + c], hi = D[L.hi + c];
+        const int il = s.side + c, iu = s.side + nc + c;
+        double a = 0.0, bb = 0.0;
+        if (lo != -INFINITY) a = lo - v + t[il];
+        if (hi != INFINITY) bb = v - hi + t[iu];
+        rd[il] = a;
+        rd[iu] = bb;
+        mx.d = fmax(mx.d, fmax(fabs(a), fabs(bb)));
+      }
+    }
+    __syncwarp();
+  }
+  (void)B;
+}
+
+struct WNorms {
+  double g, b, d, mu;
+};
+
+__device__ WNorms wresiduals(WCtx& C) {
+  const Batch& B = *C.B;
+  WMax mx{0.0, 0.0, 0.0};
+  wsweep(C, false, B.data, 8, nullptr, 0, [&](int n, const void* Dv, const void*) {
+    wres_stage(C, n, static_cast<const double*>(Dv), B.y, B.pi, B.lam, B.t, B.rg, B.rb, B.rd, false, nullptr,
+               nullptr, mx);
+  });
+  WNorms r;
+  r.g = warp_max(mx.g);
+  r.b = warp_max(mx.b);
+  r.d = warp_max(mx.d);
+  const double s = side_sum(C, [&](int i) { return B.lam[i] * B.t[i]; });
+  r.mu = C.nact ? s / C.nact : 0.0;
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// a3: square-root Riccati factorisation of one stage, lane i <-> row i.
+// Compact loops over shared-memory matrices (odd stride, conflict-free): the
+// code stays small enough for the instruction cache, which a fully unrolled
+// register version does not.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double reg) {
+  const Batch& B = *C.B;
+  const int lane = C.lane;
+  const StageDesc s = C.st[n];
+  const StageData L = wlay(s);
+  const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng, nx1 = s.nx1;
+  const int ne = welim(s, n), nk = nv - ne;
+  T* sL = static_cast<T*>(C.sL);  // L_{n+1}
+  T* sM = static_cast<T*>(C.sM);  // M rows, later X = L_ee^{-1}
+  T* sP = static_cast<T*>(C.sP);  // Phi, factorised in place
+  T* sw = reinterpret_cast<T*>(C.sv);
+  const int32_t* bmap = reinterpret_cast<const int32_t*>(D + L.box) + nb;
+  const bool act = lane < nv;
+  const int i = act ? lane : 0;
+  // barrier weights W_lo + W_hi per constraint
+  for (int c = lane; c < nc; c += 32) {
+    double w = 0.0;
+    if (D[L.lo + c] != -INFINITY) w += B.lam[s.side + c] * B.tinv[s.side + c];
+    if (D[L.hi + c] != INFINITY) w += B.lam[s.side + nc + c] * B.tinv[s.side + nc + c];
+    sw[c] = (T)w;
+  }
+  // M row i: M[i][j] = sum_{k >= j} [B A]'[i][k] L_{n+1}[k][j]
+  if (n < C.N && act) {
+    const T* ba = D + L.BAt + (int64_t)i * L.ldb;
+    for (int j = 0; j < nx1; ++j) {
+      T a0 = T(0), a1 = T(0);
+      int k = j;
+      for (; k + 1 < nx1; k += 2) {
+        a0 += ba[k] * sL[k * LDS + j];
+        a1 += ba[k + 1] * sL[(k + 1) * LDS + j];
+      }
+      if (k < nx1) a0 += ba[k] * sL[k * LDS + j];
+      sM[i * LDS + j] = a0 + a1;
+    }
+  }
+  __syncwarp();
+  // Phi row i (lower part): RSQ + M M' + [D C]' diag(w_g) [D C] + diagonal terms
+  if (act) {
+    const T* rs = D + L.RSQ + (int64_t)i * L.ldr;
+    const T* mi = sM + i * LDS;
+    const bool prod = n < C.N;
+    for (int j = 0; j <= i; ++j) {
+      const T* mj = sM + j * LDS;
+      T a0 = rs[j], a1 = T(0);
+      if (prod) {
+        int k = 0;
+        for (; k + 1 < nx1; k += 2) {
+          a0 += mi[k] * mj[k];
+          a1 += mi[k + 1] * mj[k + 1];
+        }
+        if (k < nx1) a0 += mi[k] * mj[k];
+      }
+      for (int g = 0; g < s.ng; ++g) {
+        const T* dc = D + L.DC + (int64_t)g * nv;
+        a1 += dc[i] * sw[nb + g] * dc[j];
+      }
+      sP[i * LDS + j] = a0 + a1;
+    }
+    T dadd = (T)reg;
+    if (nb > 0 && bmap[i] >= 0) dadd += sw[bmap[i]];
+    sP[i * LDS + i] += dadd;
+  }
+  __syncwarp();
+  // left-looking Cholesky in place: column k from the finished columns < k
+  bool ok = true;
+  for (int k = 0; k < nv; ++k) {
+    T sk = T(0);
+    if (act && i >= k) {
+      const T* pi_ = sP + i * LDS;
+      const T* pk = sP + k * LDS;
+      T a0 = pi_[k], a1 = T(0);
+      int p = 0;
+      for (; p + 1 < k; p += 2) {
+        a0 -= pi_[p] * pk[p];
+        a1 -= pi_[p + 1] * pk[p + 1];
+      }
+      if (p < k) a0 -= pi_[p] * pk[p];
+      sk = a0 + a1;
+    }
+    const T d = __shfl_sync(kFull, sk, k);
+    const bool good = d > T(0);
+    ok = ok && good;
+    const T r = good ? wrsqrt<T>(d) : T(1);
+    if (act && i >= k) sP[i * LDS + k] = sk * r;  // i == k: d / sqrt(d)
+    __syncwarp();
+  }
+  // X = L_ee^{-1}: lane j computes column j (entries i >= j) into sM
+  if (lane < ne) {
+    const int j = lane;
+    for (int r = j; r < ne; ++r) {
+      T acc = (r == j) ? T(1) : T(0);
+      for (int k = j; k < r; ++k) acc -= sP[r * LDS + k] * sM[k * LDS + j];
+      sM[r * LDS + j] = acc / sP[r * LDS + r];
+    }
+  }
+  __syncwarp();
+  // store the factor block (ld odd_ld(nv)): X in the leading block, L elsewhere;
+  // keep L_n = L_kk in sL
+  T* F = static_cast<T*>(B.fac) + s.fac;
+  const int ldf = odd_ld(nv);
+  for (int r = 0; r < nv; ++r) {
+    if (act) {
+      T v = T(0);
+      if (lane <= r) v = (r < ne) ? sM[r * LDS + lane] : sP[r * LDS + lane];
+      F[(int64_t)r * ldf + lane] = v;
+    }
+  }
+  for (int a = 0; a < nk; ++a)
+    if (lane < nk) sL[a * LDS + lane] = lane <= a ? sP[(ne + a) * LDS + ne + lane] : T(0);
+  __syncwarp();
+  return ok;
+}
+
+template <typename T>
+__device__ bool wfactor(WCtx& C, double reg) {
+  const Batch& B = *C.B;
+  bool ok = true;
+  const void* dbase = sizeof(T) == 8 ? static_cast<const void*>(B.data) : static_cast<const void*>(B.data32);
+  wsweep(C, true, dbase, (int)sizeof(T), nullptr, 0, [&](int n, const void* Dv, const void*) {
+    ok = wfactor_stage<T>(C, n, static_cast<const T*>(Dv), reg) && ok;
+  });
+  fence_async_global();
+  __syncwarp();
+  return ok;
+}
+
+// ---------------------------------------------------------------------------
+// a2 + a4: Riccati solve of eq. (delta) (reduced gradient per stage), then
+// dt, dlam recovered in FP64.  Returns ||(gt, r_b)||inf.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __noinline__ double wsolve(WCtx& C, const double* g, const double* rd, const double* rm, const double* rb, double* dy,
+                         double* dpi, double* dlam, double* dt) {
+  const Batch& B = *C.B;
+  const int lane = C.lane;
+  T* sL = static_cast<T*>(C.sL);
+  double* lp = B.lp;
+  const void* dbase = sizeof(T) == 8 ? static_cast<const void*>(B.data) : static_cast<const void*>(B.data32);
+  double scale = 0.0;
+  T p1 = T(0);  // p_{n+1}, element `lane`
+  wsweep(C, true, dbase, (int)sizeof(T), B.fac, (int)sizeof(T), [&](int n, const void* Dv, const void* Fv) {
+    const T* D = static_cast<const T*>(Dv);
+    const T* F = static_cast<const T*>(Fv);
+    const StageDesc s = C.st[n];
+    const StageData L = wlay(s);
+    const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng, nx1 = s.nx1;
+    const int ne = welim(s, n), nk = nv - ne;
+    const int ldf = odd_ld(nv);
+    const int32_t* bmap = reinterpret_cast<const int32_t*>(D + L.box) + nb;
+    // per-constraint v_lo - v_hi, v = (lambda r_d - r_m) / t
+    if (rd != nullptr) {
+      for (int c0 = 0; c0 < nc; c0 += 32) {
+        const int c = c0 + lane;
+        if (c < nc) {
+          const int il = s.side + c, iu = s.side + nc + c;
+          double v = 0.0;
+          if ((double)D[L.lo + c] != -INFINITY) v += (B.lam[il] * rd[il] - rm[il]) * B.tinv[il];
+          if ((double)D[L.hi + c] != INFINITY) v -= (B.lam[iu] * rd[iu] - rm[iu]) * B.tinv[iu];
+          C.sv[c] = v;
+        }
+      }
+      __syncwarp();
+    }
+    // reduced gradient element `lane`
+    double gi = 0.0;
+    if (lane < nv) {
+      gi = g[s.var + lane];
+      if (rd != nullptr) {
+        for (int gg = 0; gg < s.ng; ++gg) gi = fma(-(double)D[L.DC + (int64_t)gg * nv + lane], C.sv[nb + gg], gi);
+        if (nb > 0 && bmap[lane] >= 0) gi -= C.sv[bmap[lane]];
+      }
+      scale = fmax(scale, fabs(gi));
+    }
+    T vb = T(0);
+    if (n < C.N) {
+      const double rbd = lane < nx1 ? rb[s.eq + lane] : 0.0;
+      scale = fmax(scale, fabs(rbd));
+      const T rbl = (T)rbd;
+      // va = L_{n+1}' rb
+      T va = T(0);
+      for (int j = 0; j < nx1; ++j) {
+        const T rj = __shfl_sync(kFull, rbl, j);
+        if (j >= lane) va += sL[j * LDS + (lane < nx1 ? lane : 0)] * rj;
+      }
+      // vb = L_{n+1} va + p_{n+1}
+      vb = p1;
+      for (int j = 0; j < nx1; ++j) {
+        const T aj = __shfl_sync(kFull, va, j);
+        if (j <= lane && lane < nx1) vb += sL[lane * LDS + j] * aj;
+      }
+    }
+    // phi = gt + [B A]' vb
+    T phi = (T)gi;
+    if (n < C.N) {
+      const T* ba = D + L.BAt + (int64_t)(lane < nv ? lane : 0) * L.ldb;
+      for (int k = 0; k < nx1; ++k) phi += ba[k] * __shfl_sync(kFull, vb, k);
+    }
+    // l = X phi_e (lanes < ne)
+    T l = T(0);
+    {
+      const T* xr = F + (int64_t)(lane < ne ? lane : 0) * ldf;
+      for (int j = 0; j < ne; ++j) {
+        const T pj = __shfl_sync(kFull, phi, j);
+        if (j <= lane) l += xr[j] * pj;
+      }
+    }
+    // p_n = phi_k - L_ke l (lanes < nk)
+    T p = __shfl_sync(kFull, phi, (ne + lane) & 31);
+    {
+      const T* lr = F + (int64_t)(lane < nk ? ne + lane : 0) * ldf;
+      for (int j = 0; j < ne; ++j) p -= lr[j] * __shfl_sync(kFull, l, j);
+    }
+    if (lane < ne) lp[s.var + lane] = (double)l;
+    if (lane < nk) lp[s.var + ne + lane] = (double)p;
+    p1 = lane < nk ? p : T(0);
+    for (int a = 0; a < nk; ++a)
+      if (lane < nk) sL[a * LDS + lane] = lane <= a ? F[(int64_t)(ne + a) * ldf + ne + lane] : T(0);
+    __syncwarp();
+  });
+  // forward sweep
+  wsweep(C, false, dbase, (int)sizeof(T), B.fac, (int)sizeof(T), [&](int n, const void* Dv, const void* Fv) {
+    const T* D = static_cast<const T*>(Dv);
+    const T* F = static_cast<const T*>(Fv);
+    const StageDesc s = C.st[n];
+    const StageData L = wlay(s);
+    const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng, nx1 = s.nx1;
+    const int ne = welim(s, n), nk = nv - ne;
+    const int ldf = odd_ld(nv);
+    const int32_t* bidx = reinterpret_cast<const int32_t*>(D + L.box);
+    // x_n (lanes ne..nv-1 of the stage vector), written by the previous stage
+    const double xd = (lane >= ne && lane < nv) ? dy[s.var + lane] : 0.0;
+    const T xl = (T)xd;
+    if (n > 0) {
+      // pi_n = L_n (L_n' x_n) + p_n, L_n = L_kk
+      T w = T(0);
+      for (int j = 0; j < nk; ++j) {
+        const T xj = __shfl_sync(kFull, xl, ne + j);
+        if (j >= lane && lane < nk) w += F[(int64_t)(ne + j) * ldf + ne + lane] * xj;
+      }
+      T pk = lane < nk ? (T)lp[s.var + ne + lane] : T(0);
+      for (int j = 0; j < nk; ++j) {
+        const T wj = __shfl_sync(kFull, w, j);
+        if (j <= lane && lane < nk) pk += F[(int64_t)(ne + lane) * ldf + ne + j] * wj;
+      }
+      if (lane < nk) dpi[C.st[n - 1].eq + lane] = (double)pk;
+    }
+    // va = l + L_ke' x_n (lanes < ne)
+    T va = lane < ne ? (T)lp[s.var + lane] : T(0);
+    for (int i = 0; i < nk; ++i) {
+      const T xi = __shfl_sync(kFull, xl, ne + i);
+      if (lane < ne) va += F[(int64_t)(ne + i) * ldf + lane] * xi;
+    }
+    // u = -X' va
+    T u = T(0);
+    for (int j = 0; j < ne; ++j) {
+      const T aj = __shfl_sync(kFull, va, j);
+      if (j >= lane && lane < ne) u -= F[(int64_t)j * ldf + lane] * aj;
+    }
+    const double yd = lane < ne ? (double)u : xd;
+    if (lane < ne) dy[s.var + lane] = yd;
+    const T yl = (T)yd;
+    if (n < C.N) {
+      // x_{n+1} = [B A] y_n + rb_n
+      T acc = lane < nx1 ? (T)rb[s.eq + lane] : T(0);
+      const int kk = lane < nx1 ? lane : 0;
+      for (int i = 0; i < nv; ++i) acc += D[L.BAt + (int64_t)i * L.ldb + kk] * __shfl_sync(kFull, yl, i);
+      if (lane < nx1) dy[C.st[n + 1].var + C.st[n + 1].nu + lane] = (double)acc;
+    }
+    // dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt), FP64
+    for (int gg = 0; gg < s.ng; ++gg) {
+      const double v = gen_value<double>(C, B.data + s.data, L, nv, gg, yd);
+      if (lane == 0) C.sv[gg] = v;
+    }
+    __syncwarp();
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+      const int c = c0 + lane;
+      const int src = (c < nb) ? bidx[c] : 0;
+      const double yb = __shfl_sync(kFull, yd, src);
+      if (c < nc) {
+        const double v = c < nb ? yb : C.sv[c - nb];
+        const int il = s.side + c, iu = s.side + nc + c;
+        const double dl = rd ? rd[il] : 0.0, du = rd ? rd[iu] : 0.0;
+        const double ml = rm ? rm[il] : 0.0, mu = rm ? rm[iu] : 0.0;
+        if ((double)D[L.lo + c] != -INFINITY) {
+          const double a = v - dl;
+          dt[il] = a;
+          dlam[il] = -(ml + B.lam[il] * a) * B.tinv[il];
+        } else {
+          dt[il] = 0.0;
+          dlam[il] = 0.0;
+        }
+        if ((double)D[L.hi + c] != INFINITY) {
+          const double a = -v - du;
+          dt[iu] = a;
+          dlam[iu] = -(mu + B.lam[iu] * a) * B.tinv[iu];
+        } else {
+          dt[iu] = 0.0;
+          dlam[iu] = 0.0;
+        }
+      }
+    }
+    __syncwarp();
+  });
+  return warp_max(scale);
+}
+
+struct WDir {
+  double *dy, *dpi, *dlam, *dt;
+};
+struct WCount {
+  int ir = 0, fact = 0, fact64 = 0, solve = 0, res = 0;
+};
+
+template <typename T>
+__device__ double wnewton(WCtx& C, const WDir& d, int ir, double ir_tol, WCount* cnt) {
+  const Batch& B = *C.B;
+  const double mr = wsolve<T>(C, B.rg, B.rd, B.rm, B.rb, d.dy, d.dpi, d.dlam, d.dt);
+  ++cnt->solve;
+  if (ir <= 0) return 0.0;
+  double ratio = 0.0;
+  for (int k = 0; k <= ir; ++k) {
+    WMax mx{0.0, 0.0, 0.0};
+    wsweep(C, false, B.data, 8, nullptr, 0, [&](int n, const void* Dv, const void*) {
+      wres_stage(C, n, static_cast<const double*>(Dv), d.dy, d.dpi, d.dlam, nullptr, B.rg2, B.rb2, nullptr, true,
+                 B.rg, B.rb, mx);
+    });
+    ++cnt->res;
+    const double m = warp_max(fmax(mx.g, mx.b));
+    ratio = mr > 0.0 ? m / mr : 0.0;
+    if (k == ir || m <= ir_tol * mr) break;
+    wsolve<T>(C, B.rg2, nullptr, nullptr, B.rb2, B.dy2, B.dpi2, B.dlam2, B.dt2);
+    for (int i = C.v0 + C.lane; i < C.v1; i += 32) d.dy[i] += B.dy2[i];
+    for (int i = C.e0 + C.lane; i < C.e1; i += 32) d.dpi[i] += B.dpi2[i];
+    for (int i = C.side0 + C.lane; i < C.side0 + C.nside; i += 32) {
+      d.dlam[i] += B.dlam2[i];
+      d.dt[i] += B.dt2[i];
+    }
+    __syncwarp();
+    ++cnt->ir;
+    ++cnt->solve;
+  }
+  return ratio;
+}
+
+__device__ double wmax_step(const WCtx& C, const double* dlam, const double* dt) {
+  const Batch& B = *C.B;
+  double a = INFINITY;
+  for (int i = C.side0 + C.lane; i < C.side0 + C.nside; i += 32) {
+    if (dlam[i] < 0.0) a = fmin(a, -B.lam[i] / dlam[i]);
+    if (dt[i] < 0.0) a = fmin(a, -B.t[i] / dt[i]);
+  }
+  return warp_min(a);
+}
+
+__device__ double wmu_after(const WCtx& C, double alpha, const double* dlam, const double* dt) {
+  const Batch& B = *C.B;
+  const double s =
+      side_sum(C, [&](int i) { return (B.lam[i] + alpha * dlam[i]) * (B.t[i] + alpha * dt[i]); });
+  return C.nact ? s / C.nact : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// the kernel: one warp (one block of 32 threads) per QP
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ bool wfactor_any(WCtx& C, bool fp64, double reg) {
+  return fp64 ? wfactor<double>(C, reg) : wfactor<float>(C, reg);
+}
+
+__global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Batch B, const WarpPlan P,
+                                                      const __grid_constant__ gq_ipm_arg arg, int kind,
+                                                      double sigma_mu, const DirOut out, const int32_t* order) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int q = order[blockIdx.x];
+  const QpDesc qd = B.qp[q];
+  const int lane = threadIdx.x;
+  StageDesc* sst = reinterpret_cast<StageDesc*>(smem + P.stages);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P.bars);
+  for (int n = lane; n <= qd.N; n += 32) sst[n] = B.st[qd.stage0 + n];
+  if (lane == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_async_shared();
+  }
+  __syncwarp();
+
+  WCtx C;
+  C.B = &B;
+  C.st = sst;
+  C.N = qd.N;
+  C.nside = qd.nsidet;
+  C.side0 = qd.side0;
+  C.v0 = qd.var0;
+  C.v1 = qd.var0 + qd.nvt;
+  C.e0 = qd.eq0;
+  C.e1 = qd.eq0 + qd.neqt;
+  C.lane = lane;
+  C.ring[0] = smem + P.ring0;
+  C.ring[1] = smem + P.ring1;
+  C.bar = bars;
+  C.parity = 0;
+  C.fac_off = (uint32_t)P.fac_off;
+  C.ok = true;
+  C.sL = smem + P.sL;
+  C.sM = smem + P.sM;
+  C.sP = smem + P.sP;
+  C.sv = reinterpret_cast<double*>(smem + P.sv);
+  C.vmax = P.vmax;
+
+  // active sides (integer count, exact)
+  {
+    int cnt = 0;
+    wsweep(C, false, B.data, 8, nullptr, 0, [&](int n, const void* Dv, const void*) {
+      const double* D = static_cast<const double*>(Dv);
+      const StageDesc s = sst[n];
+      const StageData L = wlay(s);
+      const int nc = s.nbu + s.nbx + s.ng;
+      for (int c = lane; c < nc; c += 32) cnt += (D[L.lo + c] != -INFINITY) + (D[L.hi + c] != INFINITY);
+    });
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+    C.nact = cnt;
+  }
+
+  const bool mixed = arg.precision == GQ_PREC_MIXED;
+  gq_stats* stats = B.stats + q;
+  // 1/t on every side (masked sides: t = 1)
+  auto set_tinv = [&]() {
+    for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) B.tinv[i] = 1.0 / B.t[i];
+    __syncwarp();
+  };
+
+  if (kind == (int)LaunchKind::Residuals) {
+    const WNorms r = wresiduals(C);
+    if (lane == 0) {
+      stats->res[0] = r.g;
+      stats->res[1] = r.b;
+      stats->res[2] = r.d;
+      stats->res[3] = r.mu;
+      if (!C.ok) stats->status = GQ_STATUS_TIMEOUT;
+    }
+    return;
+  }
+  if (kind == (int)LaunchKind::NewtonStep) {
+    wresiduals(C);
+    for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32)
+      B.rm[i] = B.lam[i] * B.t[i] - (B.lam[i] != 0.0 ? sigma_mu : 0.0);
+    set_tinv();
+    WDir d{out.dy, out.dpi, out.dlam, out.dt};
+    WCount cnt;
+    const bool ok = mixed ? wfactor<float>(C, arg.reg_prim) : wfactor<double>(C, arg.reg_prim);
+    if (mixed)
+      wnewton<float>(C, d, arg.ir_steps, arg.ir_tol, &cnt);
+    else
+      wnewton<double>(C, d, arg.ir_steps, arg.ir_tol, &cnt);
+    if (lane == 0) {
+      stats->status = !C.ok ? GQ_STATUS_TIMEOUT : (ok ? GQ_STATUS_CONVERGED : GQ_STATUS_NAN);
+      stats->ir_total = cnt.ir;
+    }
+    return;
+  }
+
+  // ---------------- full IPM (Sec. 4.2) ----------------
+  const int64_t t_start = arg.timeout_ns > 0 ? globaltimer() : 0;
+  {
+    const bool warm1 = arg.warm_start >= 1, warm2 = arg.warm_start >= 2;
+    if (!warm1) {
+      for (int i = C.v0 + lane; i < C.v1; i += 32) B.y[i] = 0.0;
+      for (int i = C.e0 + lane; i < C.e1; i += 32) B.pi[i] = 0.0;
+    }
+    __syncwarp();
+    wsweep(C, false, B.data, 8, nullptr, 0, [&](int n, const void* Dv, const void*) {
+      const double* D = static_cast<const double*>(Dv);
+      const StageDesc s = sst[n];
+      const StageData L = wlay(s);
+      const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng;
+      const int32_t* bidx = reinterpret_cast<const int32_t*>(D + L.box);
+      const double yl = lane < nv ? B.y[s.var + lane] : 0.0;
+      for (int g = 0; g < s.ng; ++g) {
+        const double v = gen_value<double>(C, D, L, nv, g, yl);
+        if (lane == 0) C.sv[g] = v;
+      }
+      __syncwarp();
+      for (int c0 = 0; c0 < nc; c0 += 32) {
+        const int c = c0 + lane;
+        const int src = c < nb ? bidx[c] : 0;
+        const double yb = __shfl_sync(kFull, yl, src);
+        if (c < nc) {
+          const double v = c < nb ? yb : C.sv[c - nb];
+          const double lo = D[L.lo + c], hi = D[L.hi + c];
+          const int il = s.side + c, iu = s.side + nc + c;
+          if (lo != -INFINITY) {
+            if (warm2) {
+              B.lam[il] = fmax(B.lam[il], arg.warm_min);
+              B.t[il] = fmax(B.t[il], arg.warm_min);
+            } else {
+              B.lam[il] = 1.0;
+              B.t[il] = fmax(1.0, v - lo);
+            }
+          } else {
+            B.lam[il] = 0.0;
+            B.t[il] = 1.0;
+          }
+          if (hi != INFINITY) {
+            if (warm2) {
+              B.lam[iu] = fmax(B.lam[iu], arg.warm_min);
+              B.t[iu] = fmax(B.t[iu], arg.warm_min);
+            } else {
+              B.lam[iu] = 1.0;
+              B.t[iu] = fmax(1.0, hi - v);
+            }
+          } else {
+            B.lam[iu] = 0.0;
+            B.t[iu] = 1.0;
+          }
+        }
+      }
+      __syncwarp();
+    });
+  }
+
+  int status = GQ_STATUS_MAX_ITER, it = 0, flags = 0;
+  WCount cnt;
+  bool fp64 = !mixed;
+  double alpha = 1.0;
+  WNorms r{0, 0, 0, 0};
+  const WDir d{B.dy, B.dpi, B.dlam, B.dt};
+  while (true) {
+    r = wresiduals(C);
+    ++cnt.res;
+    if (!C.ok) {
+      status = GQ_STATUS_TIMEOUT;
+      break;
+    }
+    if (!(isfinite(r.g) && isfinite(r.b) && isfinite(r.d) && isfinite(r.mu))) {
+      status = GQ_STATUS_NAN;
+      break;
+    }
+    if (r.g <= arg.tol_stat && r.b <= arg.tol_eq && r.d <= arg.tol_ineq && r.mu <= arg.tol_comp) {
+      status = GQ_STATUS_CONVERGED;
+      break;
+    }
+    if (it >= arg.iter_max) {
+      status = GQ_STATUS_MAX_ITER;
+      break;
+    }
+    if (it > 0 && alpha < arg.alpha_min) {
+      status = GQ_STATUS_MIN_STEP;
+      break;
+    }
+    if (arg.timeout_ns > 0) {
+      const int64_t el = __shfl_sync(kFull, globaltimer() - t_start, 0);
+      if (el > arg.timeout_ns) {
+        status = GQ_STATUS_TIMEOUT;
+        break;
+      }
+    }
+    for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) B.rm[i] = B.lam[i] * B.t[i];
+    set_tinv();
+    const double reg = fp64 ? (mixed ? 0.0 : arg.reg_prim) : arg.reg_prim;
+    const bool ok = fp64 ? wfactor<double>(C, reg) : wfactor<float>(C, reg);
+    ++cnt.fact;
+    cnt.fact64 += fp64;
+    const bool okall = __all_sync(kFull, ok);
+    if (!okall) {
+      if (!fp64 && arg.fp64_fallback) {
+        fp64 = true;
+        flags |= GQ_FLAG_FP64_FALLBACK;
+        continue;
+      }
+      status = GQ_STATUS_NAN;
+      break;
+    }
+    if (fp64)
+      wnewton<double>(C, d, 0, 0.0, &cnt);
+    else
+      wnewton<float>(C, d, 0, 0.0, &cnt);
+    const int ir = (mixed && !fp64) || arg.mode == GQ_MODE_BALANCE ? arg.ir_steps : 0;
+    if (C.nact > 0) {
+      const double a_aff = fmin(1.0, wmax_step(C, d.dlam, d.dt));
+      const double mu_aff = wmu_after(C, a_aff, d.dlam, d.dt);
+      const double sigma = r.mu > 0.0 ? (mu_aff / r.mu) * (mu_aff / r.mu) * (mu_aff / r.mu) : 0.0;
+      const double smu = sigma * r.mu;
+      for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32)
+        B.rm[i] = B.lam[i] != 0.0 ? B.lam[i] * B.t[i] + d.dlam[i] * d.dt[i] - smu : 0.0;
+      __syncwarp();
+      double ratio = fp64 ? wnewton<double>(C, d, ir, arg.ir_tol, &cnt) : wnewton<float>(C, d, ir, arg.ir_tol, &cnt);
+      if (arg.cond_corr) {
+        const double a_c = fmin(1.0, wmax_step(C, d.dlam, d.dt));
+        const double mu_c = wmu_after(C, a_c, d.dlam, d.dt);
+        if (mu_c > arg.corr_k * mu_aff) {
+          for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32)
+            B.rm[i] = B.lam[i] != 0.0 ? B.lam[i] * B.t[i] - smu : 0.0;
+          __syncwarp();
+          ratio = fp64 ? wnewton<double>(C, d, ir, arg.ir_tol, &cnt) : wnewton<float>(C, d, ir, arg.ir_tol, &cnt);
+        }
+      }
+      if (!fp64 && arg.fp64_fallback && ir > 0 && !(ratio <= kIrFailRatio)) {
+        fp64 = true;
+        flags |= GQ_FLAG_FP64_FALLBACK;
+        continue;
+      }
+      alpha = fmin(1.0, arg.tau_b * wmax_step(C, d.dlam, d.dt));
+    } else {
+      if (ir > 0) {
+        const double ratio =
+            fp64 ? wnewton<double>(C, d, ir, arg.ir_tol, &cnt) : wnewton<float>(C, d, ir, arg.ir_tol, &cnt);
+        if (!fp64 && arg.fp64_fallback && !(ratio <= kIrFailRatio)) {
+          fp64 = true;
+          flags |= GQ_FLAG_FP64_FALLBACK;
+          continue;
+        }
+      }
+      alpha = 1.0;
+    }
+    for (int i = C.v0 + lane; i < C.v1; i += 32) B.y[i] += alpha * d.dy[i];
+    for (int i = C.e0 + lane; i < C.e1; i += 32) B.pi[i] += alpha * d.dpi[i];
+    for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) {
+      if (B.lam[i] != 0.0 || d.dlam[i] != 0.0) {
+        B.lam[i] = fmax(B.lam[i] + alpha * d.dlam[i], arg.lam_min);
+        B.t[i] = fmax(B.t[i] + alpha * d.dt[i], arg.t_min);
+      }
+    }
+    __syncwarp();
+    ++it;
+  }
+  if (lane == 0) {
+    stats->status = status;
+    stats->iters = it;
+    stats->flags = flags;
+    stats->ir_total = cnt.ir;
+    stats->n_fact = cnt.fact;
+    stats->n_fact64 = cnt.fact64;
+    stats->n_solve = cnt.solve;
+    stats->n_res = cnt.res;
+    stats->res[0] = r.g;
+    stats->res[1] = r.b;
+    stats->res[2] = r.d;
+    stats->res[3] = r.mu;
+  }
+}
+
+// FP32 mirror of the stage data blocks: values converted, box indices copied
+__global__ void mirror_kernel(const __grid_constant__ Batch B) {
+  for (int sl = blockIdx.x; sl < B.nslots; sl += gridDim.x) {
+    const StageDesc s = B.st[B.slots[sl]];
+    const StageData L = wlay(s);
+    const double* src = B.data + s.data;
+    float* dst = B.data32 + s.data;
+    for (int64_t i = threadIdx.x; i < L.box; i += blockDim.x) dst[i] = (float)src[i];
+    const int32_t* si = reinterpret_cast<const int32_t*>(src + L.box);
+    int32_t* di = reinterpret_cast<int32_t*>(dst + L.box);
+    const int nint = s.nbu + s.nbx + s.nx + s.nu;
+    for (int i = threadIdx.x; i < nint; i += blockDim.x) di[i] = si[i];
+  }
+}
+
+}  // namespace
+
+WarpPlan warp_plan(const Batch& b, const Shape& sh, int precision) {
+  WarpPlan p;
+  size_t o = 0;
+  auto take = [&](size_t bytes, size_t align) {
+    o = (o + align - 1) / align * align;
+    const size_t at = o;
+    o += bytes;
+    return at;
+  };
+  const size_t te = precision == GQ_PREC_MIXED ? 4 : 8;
+  p.vmax = sh.nvmax + sh.ngmax + 2 > 64 ? sh.nvmax + sh.ngmax + 2 : 64;
+  p.bars = take(2 * sizeof(uint64_t), 16);
+  p.stages = take((size_t)sh.nst_max * sizeof(StageDesc), 16);
+  // FP64 fallback needs the double-width matrices even on the mixed path
+  p.sL = take(32 * LDS * 8, 16);
+  p.sM = take(32 * LDS * 8, 16);
+  p.sP = take(32 * LDS * 8, 16);
+  p.sv = take((size_t)p.vmax * 8, 16);
+  // ring slot: FP64 data block, or a factor-width data block + factor block
+  const size_t d64 = (size_t)sh.data_max * 8;
+  const size_t f64 = (size_t)fac_block_elems(sh.nvmax) * 8;
+  p.fac_off = (size_t)sh.data_max * 8;  // fits both the FP32 and FP64 data blocks
+  p.fac_off = (p.fac_off + 127) / 128 * 128;
+  size_t slot = p.fac_off + f64;
+  if (slot < d64) slot = d64;
+  slot = (slot + 127) / 128 * 128;
+  (void)te;
+  p.ring0 = take(slot, 128);
+  p.ring1 = take(slot, 128);
+  p.bytes = o;
+  return p;
+}
+
+cudaError_t launch_warp_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
+                            LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count) {
+  if (count <= 0) return cudaSuccess;
+  if (arg.precision == GQ_PREC_MIXED) {
+    int grid = b.nslots < 4096 ? b.nslots : 4096;
+    if (grid < 1) grid = 1;
+    mirror_kernel<<<grid, 128, 0, stream>>>(b);
+  }
+  const WarpPlan P = warp_plan(b, sh, arg.precision);
+  static size_t attr_bytes = 48 * 1024;
+  if (P.bytes > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(warp_ipm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.bytes);
+    if (e != cudaSuccess) return e;
+    attr_bytes = P.bytes;
+  }
+  DirOut o{};
+  if (out) o = *out;
+  warp_ipm_kernel<<<count, 32, P.bytes, stream>>>(b, P, arg, (int)kind, sigma_mu, o, order);
+  return cudaGetLastError();
+}
+
+}  // namespace gq
