@@ -214,6 +214,28 @@ GQ_API int gq_solve(gq_batch* b, const gq_ipm_arg* arg, void* stream);
 GQ_API int gq_residuals(gq_batch* b, void* stream);
 GQ_API int gq_newton_step(gq_batch* b, const gq_ipm_arg* arg, double sigma_mu, void* dev_dir, void* stream);
 
+/* ---- solve without allocation (no counterpart in the paper) ----
+ * For callers that cannot allocate device memory when they solve (a fixed
+ * memory budget, an allocator owned by a host application, or a region where
+ * allocation would synchronise).  Same arguments and results as gq_solve, but
+ * the input and solution buffers are passed here and the workspace is a
+ * file-scope device array of GQ_NOALLOC_SCRATCH_BYTES inside the library,
+ * held by every GPU that loads the library until the process exits.
+ *   - dev_in / dev_sol: 256-byte aligned device buffers of sizes.in_bytes and
+ *     sizes.sol_bytes laid out as for gq_solve (gq_upload / gq_download use the
+ *     attached buffers; copy into these with cudaMemcpyAsync when they differ).
+ *   - Returns GQ_ERR_SIZE, before any GPU work, when sizes.ws_bytes exceeds
+ *     GQ_NOALLOC_SCRATCH_BYTES.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.  The first
+ *     call on each device looks up the array's device address (with that
+ *     device current); make that first call before any stream capture.
+ *   - Every call shares the one array and leaves its contents behind; the
+ *     solver writes every workspace entry before reading it, so nothing needs
+ *     clearing.  Calls whose GPU work overlaps (other streams, other threads)
+ *     race on the array: serialise them. */
+#define GQ_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+GQ_API int gq_solve_noalloc(gq_batch* b, const gq_ipm_arg* arg, void* dev_in, void* dev_sol, void* stream);
+
 /* ---- getters (read host_sol after gq_download + stream sync) ---- */
 /* u: nu_n, x: nx_n, pi: nx_{n+1} (n < N; multiplier of dynamics block n),
  * lam, t: 2 nc_n.  Any pointer may be NULL. */

@@ -768,3 +768,74 @@ int gq_get_sol_offsets(const gq_batch* b, int qp, int64_t off[8]) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Solve without any device allocation by the caller or the library.
+//
+// For callers that cannot allocate device memory at solve time: code running
+// under a fixed memory budget that forbids runtime allocation (safety-critical
+// embedded controllers), plug-ins whose host application owns the allocator,
+// or solves issued from inside a region where allocation would synchronise or
+// fail.  They still pass the input and solution buffers; the workspace comes
+// from one file-scope device array of GQ_NOALLOC_SCRATCH_BYTES, which every
+// GPU that loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GQ_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// device address of the scratch array on the current device (set-up on the
+// first call per device; the host-side name is only a stand-in)
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(GQ_ERR_ARG, "noalloc: device index %d unsupported", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GQ_OK;
+}
+
+}  // namespace
+
+extern "C" int gq_solve_noalloc(gq_batch* b, const gq_ipm_arg* arg, void* dev_in, void* dev_sol, void* stream) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  rc = check_arg(arg);
+  if (rc) return rc;
+  if (dev_in == nullptr || dev_sol == nullptr) return fail(GQ_ERR_ARG, "noalloc: dev_in and dev_sol must be non-NULL");
+  if (reinterpret_cast<uintptr_t>(dev_in) % 256 || reinterpret_cast<uintptr_t>(dev_sol) % 256)
+    return fail(GQ_ERR_ARG, "noalloc: device buffers must be 256-byte aligned");
+  if (b->sizes.ws_bytes > (size_t)GQ_NOALLOC_SCRATCH_BYTES)
+    return fail(GQ_ERR_SIZE, "noalloc: batch needs %zu workspace bytes, the static scratch holds %zu (use gq_solve)",
+                b->sizes.ws_bytes, (size_t)GQ_NOALLOC_SCRATCH_BYTES);
+  void* ws = nullptr;
+  rc = noalloc_scratch(&ws);
+  if (rc) return rc;
+  // the same kernel arguments as gq_solve, with the static scratch as workspace
+  void* saved[3] = {b->dev_in, b->dev_sol, b->dev_ws};
+  b->dev_in = dev_in;
+  b->dev_sol = dev_sol;
+  b->dev_ws = ws;
+  Batch k;
+  rc = make_kernel_batch(b, &k);
+  b->dev_in = saved[0];
+  b->dev_sol = saved[1];
+  b->dev_ws = saved[2];
+  if (rc) return rc;
+  cudaError_t e = launch_all(b, k, *arg, static_cast<cudaStream_t>(stream), LaunchKind::Solve, 0.0, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "noalloc solve launch");
+  return GQ_OK;
+}

@@ -17,6 +17,7 @@ STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_MIN_STEP, STATUS_NAN, STATUS_TIMEOUT =
 FLAG_FP64_FALLBACK = 1
 MODE_SPEED, MODE_BALANCE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 c_int, c_int64, c_double, c_size_t, c_void_p = (ctypes.c_int, ctypes.c_int64, ctypes.c_double,
                                                 ctypes.c_size_t, ctypes.c_void_p)
@@ -66,6 +67,7 @@ SIGNATURES = {
     "gq_solve": (c_int, [c_void_p, ctypes.POINTER(IpmArg), c_void_p]),
     "gq_residuals": (c_int, [c_void_p, c_void_p]),
     "gq_newton_step": (c_int, [c_void_p, ctypes.POINTER(IpmArg), c_double, c_void_p, c_void_p]),
+    "gq_solve_noalloc": (c_int, [c_void_p, ctypes.POINTER(IpmArg), c_void_p, c_void_p, c_void_p]),
     "gq_get_stage_sol": (c_int, [c_void_p, c_int, c_int, P_double, P_double, P_double, P_double, P_double]),
     "gq_get_stats": (c_int, [c_void_p, c_int, ctypes.POINTER(Stats)]),
     "gq_get_sol_offsets": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64)]),
