@@ -644,7 +644,7 @@ static int make_kernel_batch(gq_batch* b, Batch* k) {
                   b->shape_b.nvmax, b->shape_b.nxmax, smem, kMaxSmem);
   }
   if (b->nwarp > 0) {
-    const size_t smem = warp_plan(*k, b->shape_w, GQ_PREC_FP64).bytes;
+    const size_t smem = warp_plan(*k, b->shape_w, 8).bytes;
     if (smem > kMaxSmem)
       return fail(GQ_ERR_DIMS, "warp bucket needs %zu bytes of shared memory per block (limit %zu)", smem, kMaxSmem);
   }

@@ -6,7 +6,7 @@
 
 namespace gq {
 
-enum class LaunchKind { Solve, Residuals, NewtonStep };
+enum class LaunchKind { Solve, Residuals, NewtonStep, Resume };
 
 // Output of a single Newton direction (row-level entry point).
 struct DirOut {
@@ -30,7 +30,7 @@ struct WarpPlan {
   size_t bars, stages, sL, sM, sP, sv, ring0, ring1, fac_off, bytes;
   int vmax;
 };
-WarpPlan warp_plan(const Batch& b, const Shape& sh, int precision);
+WarpPlan warp_plan(const Batch& b, const Shape& sh, int elem);  // elem: factor element size
 cudaError_t launch_warp_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
                             LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count);
 

@@ -127,7 +127,7 @@ struct WMax {
   double g, b, d;
 };
 
-__device__ __noinline__ void wres_stage(WCtx& C, int n, const double* D, const double* y, const double* pi, const double* lam,
+__device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, const double* y, const double* pi, const double* lam,
                            const double* t, double* og, double* ob, double* rd, bool lin, const double* add_g,
                            const double* add_b, WMax& mx) {
   const Batch& B = *C.B;
@@ -145,6 +145,7 @@ __device__ __noinline__ void wres_stage(WCtx& C, int n, const double* D, const d
     const double* row = D + L.RSQ + (int64_t)(lane < nv ? lane : 0) * L.ldr;
     double a0 = 0.0, a1 = 0.0;
     int j = 0;
+#pragma unroll 2
     for (; j + 1 < nv; j += 2) {
       const double y0 = __shfl_sync(kFull, yl, j), y1 = __shfl_sync(kFull, yl, j + 1);
       a0 = fma(row[j], y0, a0);
@@ -154,6 +155,7 @@ __device__ __noinline__ void wres_stage(WCtx& C, int n, const double* D, const d
     if (n < C.N) {
       const double* ba = D + L.BAt + (int64_t)(lane < nv ? lane : 0) * L.ldb;
       int k = 0;
+#pragma unroll 2
       for (; k + 1 < nx1; k += 2) {
         const double p0 = __shfl_sync(kFull, pl, k), p1 = __shfl_sync(kFull, pl, k + 1);
         a0 = fma(ba[k], p0, a0);
@@ -178,6 +180,7 @@ __device__ __noinline__ void wres_stage(WCtx& C, int n, const double* D, const d
     double a0 = 0.0, a1 = 0.0;
     const int kk = lane < nx1 ? lane : 0;
     int i = 0;
+#pragma unroll 2
     for (; i + 1 < nv; i += 2) {
       const double y0 = __shfl_sync(kFull, yl, i), y1 = __shfl_sync(kFull, yl, i + 1);
       a0 = fma(D[L.BAt + (int64_t)i * L.ldb + kk], y0, a0);
@@ -246,7 +249,7 @@ __device__ WNorms wresiduals(WCtx& C) {
 // register version does not.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __noinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double reg) {
+__device__ __forceinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double reg) {
   const Batch& B = *C.B;
   const int lane = C.lane;
   const StageDesc s = C.st[n];
@@ -271,14 +274,16 @@ __device__ __noinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double re
   if (n < C.N && act) {
     const T* ba = D + L.BAt + (int64_t)i * L.ldb;
     for (int j = 0; j < nx1; ++j) {
-      T a0 = T(0), a1 = T(0);
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
       int k = j;
-      for (; k + 1 < nx1; k += 2) {
+      for (; k + 3 < nx1; k += 4) {
         a0 += ba[k] * sL[k * LDS + j];
         a1 += ba[k + 1] * sL[(k + 1) * LDS + j];
+        a2 += ba[k + 2] * sL[(k + 2) * LDS + j];
+        a3 += ba[k + 3] * sL[(k + 3) * LDS + j];
       }
-      if (k < nx1) a0 += ba[k] * sL[k * LDS + j];
-      sM[i * LDS + j] = a0 + a1;
+      for (; k < nx1; ++k) a0 += ba[k] * sL[k * LDS + j];
+      sM[i * LDS + j] = (a0 + a1) + (a2 + a3);
     }
   }
   __syncwarp();
@@ -289,15 +294,19 @@ __device__ __noinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double re
     const bool prod = n < C.N;
     for (int j = 0; j <= i; ++j) {
       const T* mj = sM + j * LDS;
-      T a0 = rs[j], a1 = T(0);
+      T a0 = rs[j], a1 = T(0), a2 = T(0), a3 = T(0);
       if (prod) {
         int k = 0;
-        for (; k + 1 < nx1; k += 2) {
+        for (; k + 3 < nx1; k += 4) {
           a0 += mi[k] * mj[k];
           a1 += mi[k + 1] * mj[k + 1];
+          a2 += mi[k + 2] * mj[k + 2];
+          a3 += mi[k + 3] * mj[k + 3];
         }
-        if (k < nx1) a0 += mi[k] * mj[k];
+        for (; k < nx1; ++k) a0 += mi[k] * mj[k];
       }
+      a0 = (a0 + a1) + (a2 + a3);
+      a1 = T(0);
       for (int g = 0; g < s.ng; ++g) {
         const T* dc = D + L.DC + (int64_t)g * nv;
         a1 += dc[i] * sw[nb + g] * dc[j];
@@ -316,14 +325,16 @@ __device__ __noinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double re
     if (act && i >= k) {
       const T* pi_ = sP + i * LDS;
       const T* pk = sP + k * LDS;
-      T a0 = pi_[k], a1 = T(0);
+      T a0 = pi_[k], a1 = T(0), a2 = T(0), a3 = T(0);
       int p = 0;
-      for (; p + 1 < k; p += 2) {
+      for (; p + 3 < k; p += 4) {
         a0 -= pi_[p] * pk[p];
         a1 -= pi_[p + 1] * pk[p + 1];
+        a2 -= pi_[p + 2] * pk[p + 2];
+        a3 -= pi_[p + 3] * pk[p + 3];
       }
-      if (p < k) a0 -= pi_[p] * pk[p];
-      sk = a0 + a1;
+      for (; p < k; ++p) a0 -= pi_[p] * pk[p];
+      sk = (a0 + a1) + (a2 + a3);
     }
     const T d = __shfl_sync(kFull, sk, k);
     const bool good = d > T(0);
@@ -377,7 +388,7 @@ __device__ bool wfactor(WCtx& C, double reg) {
 // dt, dlam recovered in FP64.  Returns ||(gt, r_b)||inf.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __noinline__ double wsolve(WCtx& C, const double* g, const double* rd, const double* rm, const double* rb, double* dy,
+__device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double* rd, const double* rm, const double* rb, double* dy,
                          double* dpi, double* dlam, double* dt) {
   const Batch& B = *C.B;
   const int lane = C.lane;
@@ -426,12 +437,14 @@ __device__ __noinline__ double wsolve(WCtx& C, const double* g, const double* rd
       const T rbl = (T)rbd;
       // va = L_{n+1}' rb
       T va = T(0);
+      #pragma unroll 4
       for (int j = 0; j < nx1; ++j) {
         const T rj = __shfl_sync(kFull, rbl, j);
         if (j >= lane) va += sL[j * LDS + (lane < nx1 ? lane : 0)] * rj;
       }
       // vb = L_{n+1} va + p_{n+1}
       vb = p1;
+      #pragma unroll 4
       for (int j = 0; j < nx1; ++j) {
         const T aj = __shfl_sync(kFull, va, j);
         if (j <= lane && lane < nx1) vb += sL[lane * LDS + j] * aj;
@@ -441,12 +454,22 @@ __device__ __noinline__ double wsolve(WCtx& C, const double* g, const double* rd
     T phi = (T)gi;
     if (n < C.N) {
       const T* ba = D + L.BAt + (int64_t)(lane < nv ? lane : 0) * L.ldb;
-      for (int k = 0; k < nx1; ++k) phi += ba[k] * __shfl_sync(kFull, vb, k);
+            T ph2 = T(0);
+      int k = 0;
+#pragma unroll 2
+      for (; k + 1 < nx1; k += 2) {
+        const T v0 = __shfl_sync(kFull, vb, k), v1 = __shfl_sync(kFull, vb, k + 1);
+        phi += ba[k] * v0;
+        ph2 += ba[k + 1] * v1;
+      }
+      if (k < nx1) phi += ba[k] * __shfl_sync(kFull, vb, k);
+      phi += ph2;
     }
     // l = X phi_e (lanes < ne)
     T l = T(0);
     {
       const T* xr = F + (int64_t)(lane < ne ? lane : 0) * ldf;
+      #pragma unroll 4
       for (int j = 0; j < ne; ++j) {
         const T pj = __shfl_sync(kFull, phi, j);
         if (j <= lane) l += xr[j] * pj;
@@ -456,6 +479,7 @@ __device__ __noinline__ double wsolve(WCtx& C, const double* g, const double* rd
     T p = __shfl_sync(kFull, phi, (ne + lane) & 31);
     {
       const T* lr = F + (int64_t)(lane < nk ? ne + lane : 0) * ldf;
+      #pragma unroll 4
       for (int j = 0; j < ne; ++j) p -= lr[j] * __shfl_sync(kFull, l, j);
     }
     if (lane < ne) lp[s.var + lane] = (double)l;
@@ -481,11 +505,13 @@ __device__ __noinline__ double wsolve(WCtx& C, const double* g, const double* rd
     if (n > 0) {
       // pi_n = L_n (L_n' x_n) + p_n, L_n = L_kk
       T w = T(0);
+      #pragma unroll 4
       for (int j = 0; j < nk; ++j) {
         const T xj = __shfl_sync(kFull, xl, ne + j);
         if (j >= lane && lane < nk) w += F[(int64_t)(ne + j) * ldf + ne + lane] * xj;
       }
       T pk = lane < nk ? (T)lp[s.var + ne + lane] : T(0);
+      #pragma unroll 4
       for (int j = 0; j < nk; ++j) {
         const T wj = __shfl_sync(kFull, w, j);
         if (j <= lane && lane < nk) pk += F[(int64_t)(ne + lane) * ldf + ne + j] * wj;
@@ -494,12 +520,14 @@ __device__ __noinline__ double wsolve(WCtx& C, const double* g, const double* rd
     }
     // va = l + L_ke' x_n (lanes < ne)
     T va = lane < ne ? (T)lp[s.var + lane] : T(0);
+    #pragma unroll 4
     for (int i = 0; i < nk; ++i) {
       const T xi = __shfl_sync(kFull, xl, ne + i);
       if (lane < ne) va += F[(int64_t)(ne + i) * ldf + lane] * xi;
     }
     // u = -X' va
     T u = T(0);
+    #pragma unroll 4
     for (int j = 0; j < ne; ++j) {
       const T aj = __shfl_sync(kFull, va, j);
       if (j >= lane && lane < ne) u -= F[(int64_t)j * ldf + lane] * aj;
@@ -511,7 +539,16 @@ __device__ __noinline__ double wsolve(WCtx& C, const double* g, const double* rd
       // x_{n+1} = [B A] y_n + rb_n
       T acc = lane < nx1 ? (T)rb[s.eq + lane] : T(0);
       const int kk = lane < nx1 ? lane : 0;
-      for (int i = 0; i < nv; ++i) acc += D[L.BAt + (int64_t)i * L.ldb + kk] * __shfl_sync(kFull, yl, i);
+            T acc2 = T(0);
+      int i = 0;
+#pragma unroll 2
+      for (; i + 1 < nv; i += 2) {
+        const T y0 = __shfl_sync(kFull, yl, i), y1 = __shfl_sync(kFull, yl, i + 1);
+        acc += D[L.BAt + (int64_t)i * L.ldb + kk] * y0;
+        acc2 += D[L.BAt + (int64_t)(i + 1) * L.ldb + kk] * y1;
+      }
+      if (i < nv) acc += D[L.BAt + (int64_t)i * L.ldb + kk] * __shfl_sync(kFull, yl, i);
+      acc += acc2;
       if (lane < nx1) dy[C.st[n + 1].var + C.st[n + 1].nu + lane] = (double)acc;
     }
     // dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt), FP64
@@ -610,16 +647,18 @@ __device__ double wmu_after(const WCtx& C, double alpha, const double* dlam, con
 // ---------------------------------------------------------------------------
 // the kernel: one warp (one block of 32 threads) per QP
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ bool wfactor_any(WCtx& C, bool fp64, double reg) {
-  return fp64 ? wfactor<double>(C, reg) : wfactor<float>(C, reg);
-}
+// QP status while a mixed-precision solve hands over to the FP64 resume launch
+constexpr int kStatusResumeFp64 = 100;
 
+template <typename T>
 __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Batch B, const WarpPlan P,
                                                       const __grid_constant__ gq_ipm_arg arg, int kind,
                                                       double sigma_mu, const DirOut out, const int32_t* order) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int q = order[blockIdx.x];
+  gq_stats* stats = B.stats + q;
+  const bool resume = kind == (int)LaunchKind::Resume;
+  if (resume && stats->status != kStatusResumeFp64) return;  // uniform across the warp
   const QpDesc qd = B.qp[q];
   const int lane = threadIdx.x;
   StageDesc* sst = reinterpret_cast<StageDesc*>(smem + P.stages);
@@ -671,7 +710,6 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
   }
 
   const bool mixed = arg.precision == GQ_PREC_MIXED;
-  gq_stats* stats = B.stats + q;
   // 1/t on every side (masked sides: t = 1)
   auto set_tinv = [&]() {
     for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) B.tinv[i] = 1.0 / B.t[i];
@@ -696,11 +734,8 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
     set_tinv();
     WDir d{out.dy, out.dpi, out.dlam, out.dt};
     WCount cnt;
-    const bool ok = mixed ? wfactor<float>(C, arg.reg_prim) : wfactor<double>(C, arg.reg_prim);
-    if (mixed)
-      wnewton<float>(C, d, arg.ir_steps, arg.ir_tol, &cnt);
-    else
-      wnewton<double>(C, d, arg.ir_steps, arg.ir_tol, &cnt);
+    const bool ok = wfactor<T>(C, arg.reg_prim);
+    wnewton<T>(C, d, arg.ir_steps, arg.ir_tol, &cnt);
     if (lane == 0) {
       stats->status = !C.ok ? GQ_STATUS_TIMEOUT : (ok ? GQ_STATUS_CONVERGED : GQ_STATUS_NAN);
       stats->ir_total = cnt.ir;
@@ -710,7 +745,7 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
 
   // ---------------- full IPM (Sec. 4.2) ----------------
   const int64_t t_start = arg.timeout_ns > 0 ? globaltimer() : 0;
-  {
+  if (!resume) {
     const bool warm1 = arg.warm_start >= 1, warm2 = arg.warm_start >= 2;
     if (!warm1) {
       for (int i = C.v0 + lane; i < C.v1; i += 32) B.y[i] = 0.0;
@@ -767,9 +802,20 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
     });
   }
 
+  // a mixed solve runs with T = float; T = double is the plain FP64 solve or
+  // the FP64 continuation of mixed QPs whose refinement stagnated
+  const bool fp64 = sizeof(T) == 8;
   int status = GQ_STATUS_MAX_ITER, it = 0, flags = 0;
   WCount cnt;
-  bool fp64 = !mixed;
+  if (resume) {
+    it = stats->iters;
+    flags = stats->flags | GQ_FLAG_FP64_FALLBACK;
+    cnt.ir = stats->ir_total;
+    cnt.fact = stats->n_fact;
+    cnt.fact64 = stats->n_fact64;
+    cnt.solve = stats->n_solve;
+    cnt.res = stats->n_res;
+  }
   double alpha = 1.0;
   WNorms r{0, 0, 0, 0};
   const WDir d{B.dy, B.dpi, B.dlam, B.dt};
@@ -806,23 +852,19 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
     for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) B.rm[i] = B.lam[i] * B.t[i];
     set_tinv();
     const double reg = fp64 ? (mixed ? 0.0 : arg.reg_prim) : arg.reg_prim;
-    const bool ok = fp64 ? wfactor<double>(C, reg) : wfactor<float>(C, reg);
+    const bool ok = wfactor<T>(C, reg);
     ++cnt.fact;
     cnt.fact64 += fp64;
     const bool okall = __all_sync(kFull, ok);
     if (!okall) {
       if (!fp64 && arg.fp64_fallback) {
-        fp64 = true;
-        flags |= GQ_FLAG_FP64_FALLBACK;
-        continue;
+        status = kStatusResumeFp64;
+        break;
       }
       status = GQ_STATUS_NAN;
       break;
     }
-    if (fp64)
-      wnewton<double>(C, d, 0, 0.0, &cnt);
-    else
-      wnewton<float>(C, d, 0, 0.0, &cnt);
+    wnewton<T>(C, d, 0, 0.0, &cnt);
     const int ir = (mixed && !fp64) || arg.mode == GQ_MODE_BALANCE ? arg.ir_steps : 0;
     if (C.nact > 0) {
       const double a_aff = fmin(1.0, wmax_step(C, d.dlam, d.dt));
@@ -832,7 +874,7 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
       for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32)
         B.rm[i] = B.lam[i] != 0.0 ? B.lam[i] * B.t[i] + d.dlam[i] * d.dt[i] - smu : 0.0;
       __syncwarp();
-      double ratio = fp64 ? wnewton<double>(C, d, ir, arg.ir_tol, &cnt) : wnewton<float>(C, d, ir, arg.ir_tol, &cnt);
+      double ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
       if (arg.cond_corr) {
         const double a_c = fmin(1.0, wmax_step(C, d.dlam, d.dt));
         const double mu_c = wmu_after(C, a_c, d.dlam, d.dt);
@@ -840,23 +882,22 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
           for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32)
             B.rm[i] = B.lam[i] != 0.0 ? B.lam[i] * B.t[i] - smu : 0.0;
           __syncwarp();
-          ratio = fp64 ? wnewton<double>(C, d, ir, arg.ir_tol, &cnt) : wnewton<float>(C, d, ir, arg.ir_tol, &cnt);
+          ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
         }
       }
       if (!fp64 && arg.fp64_fallback && ir > 0 && !(ratio <= kIrFailRatio)) {
-        fp64 = true;
-        flags |= GQ_FLAG_FP64_FALLBACK;
-        continue;
+        // refinement could not recover the FP32 factors' accuracy: the FP64
+        // launch continues this QP from the current iterate
+        status = kStatusResumeFp64;
+        break;
       }
       alpha = fmin(1.0, arg.tau_b * wmax_step(C, d.dlam, d.dt));
     } else {
       if (ir > 0) {
-        const double ratio =
-            fp64 ? wnewton<double>(C, d, ir, arg.ir_tol, &cnt) : wnewton<float>(C, d, ir, arg.ir_tol, &cnt);
+        const double ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
         if (!fp64 && arg.fp64_fallback && !(ratio <= kIrFailRatio)) {
-          fp64 = true;
-          flags |= GQ_FLAG_FP64_FALLBACK;
-          continue;
+          status = kStatusResumeFp64;
+          break;
         }
       }
       alpha = 1.0;
@@ -905,7 +946,8 @@ __global__ void mirror_kernel(const __grid_constant__ Batch B) {
 
 }  // namespace
 
-WarpPlan warp_plan(const Batch& b, const Shape& sh, int precision) {
+WarpPlan warp_plan(const Batch& b, const Shape& sh, int elem) {
+  (void)b;
   WarpPlan p;
   size_t o = 0;
   auto take = [&](size_t bytes, size_t align) {
@@ -914,49 +956,56 @@ WarpPlan warp_plan(const Batch& b, const Shape& sh, int precision) {
     o += bytes;
     return at;
   };
-  const size_t te = precision == GQ_PREC_MIXED ? 4 : 8;
-  p.vmax = sh.nvmax + sh.ngmax + 2 > 64 ? sh.nvmax + sh.ngmax + 2 : 64;
+  const size_t te = (size_t)elem;  // factor precision: 4 (mixed) or 8 (FP64)
+  const int nv = sh.nvmax > 0 ? sh.nvmax : 1, nx = sh.nxmax > 0 ? sh.nxmax : 1;
+  p.vmax = sh.nvmax + sh.ngmax + 2 > 32 ? sh.nvmax + sh.ngmax + 2 : 32;
   p.bars = take(2 * sizeof(uint64_t), 16);
   p.stages = take((size_t)sh.nst_max * sizeof(StageDesc), 16);
-  // FP64 fallback needs the double-width matrices even on the mixed path
-  p.sL = take(32 * LDS * 8, 16);
-  p.sM = take(32 * LDS * 8, 16);
-  p.sP = take(32 * LDS * 8, 16);
+  p.sL = take((size_t)nx * LDS * te, 16);
+  p.sM = take((size_t)nv * LDS * te, 16);
+  p.sP = take((size_t)nv * LDS * te, 16);
   p.sv = take((size_t)p.vmax * 8, 16);
-  // ring slot: FP64 data block, or a factor-width data block + factor block
+  // ring slot: the FP64 data block (residual sweeps), or a factor-precision
+  // data block followed by a factor block (factorisation and solves)
+  p.fac_off = ((size_t)sh.data_max * te + 127) / 128 * 128;
+  size_t slot = p.fac_off + (size_t)fac_block_elems(sh.nvmax) * te;
   const size_t d64 = (size_t)sh.data_max * 8;
-  const size_t f64 = (size_t)fac_block_elems(sh.nvmax) * 8;
-  p.fac_off = (size_t)sh.data_max * 8;  // fits both the FP32 and FP64 data blocks
-  p.fac_off = (p.fac_off + 127) / 128 * 128;
-  size_t slot = p.fac_off + f64;
   if (slot < d64) slot = d64;
   slot = (slot + 127) / 128 * 128;
-  (void)te;
   p.ring0 = take(slot, 128);
   p.ring1 = take(slot, 128);
   p.bytes = o;
   return p;
 }
 
-cudaError_t launch_warp_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
-                            LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count) {
-  if (count <= 0) return cudaSuccess;
-  if (arg.precision == GQ_PREC_MIXED) {
-    int grid = b.nslots < 4096 ? b.nslots : 4096;
-    if (grid < 1) grid = 1;
-    mirror_kernel<<<grid, 128, 0, stream>>>(b);
-  }
-  const WarpPlan P = warp_plan(b, sh, arg.precision);
+template <typename T>
+static cudaError_t launch_one(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
+                              LaunchKind kind, double sigma_mu, const DirOut& o, const int32_t* order, int count) {
+  const WarpPlan P = warp_plan(b, sh, (int)sizeof(T));
   static size_t attr_bytes = 48 * 1024;
   if (P.bytes > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(warp_ipm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.bytes);
+    cudaError_t e = cudaFuncSetAttribute(warp_ipm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.bytes);
     if (e != cudaSuccess) return e;
     attr_bytes = P.bytes;
   }
+  warp_ipm_kernel<T><<<count, 32, P.bytes, stream>>>(b, P, arg, (int)kind, sigma_mu, o, order);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_warp_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
+                            LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count) {
+  if (count <= 0) return cudaSuccess;
   DirOut o{};
   if (out) o = *out;
-  warp_ipm_kernel<<<count, 32, P.bytes, stream>>>(b, P, arg, (int)kind, sigma_mu, o, order);
-  return cudaGetLastError();
+  if (arg.precision != GQ_PREC_MIXED || kind == LaunchKind::Residuals)
+    return launch_one<double>(b, sh, arg, stream, kind, sigma_mu, o, order, count);
+  int grid = b.nslots < 4096 ? b.nslots : 4096;
+  if (grid < 1) grid = 1;
+  mirror_kernel<<<grid, 128, 0, stream>>>(b);
+  cudaError_t e = launch_one<float>(b, sh, arg, stream, kind, sigma_mu, o, order, count);
+  if (e != cudaSuccess || kind != LaunchKind::Solve || !arg.fp64_fallback) return e;
+  // FP64 continuation of the QPs whose FP32 factors were not accurate enough
+  return launch_one<double>(b, sh, arg, stream, LaunchKind::Resume, sigma_mu, o, order, count);
 }
 
 }  // namespace gq
