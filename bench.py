@@ -168,6 +168,15 @@ def cpu_oracle(sample: int, offset: int = 0):
 
 
 # ----------------------------------------------------------------------------
+def launches_per_solve(qps, arg) -> int:
+    """Kernel launches of one mixed gq_solve: QPs whose stages fit one warp
+    run in the FP32 mirror copy, the mixed warp kernel and its FP64
+    continuation launch; larger QPs in one block kernel launch."""
+    warp = any(max(q.nx[n] + q.nu[n] for n in range(q.N + 1)) <= 32 and max(q.nx) <= 32 for q in qps)
+    block = any(not (max(q.nx[n] + q.nu[n] for n in range(q.N + 1)) <= 32 and max(q.nx) <= 32) for q in qps)
+    return (3 if arg.fp64_fallback else 2) * warp + block
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -255,7 +264,7 @@ def main():
     barrier()
     ck = clocks.stop()
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-    launches = a.steps                      # one IPM kernel launch per step
+    launches = a.steps * launches_per_solve(qps, arg_mixed)
     b.download()
     torch.cuda.synchronize()
     st = b.all_stats()
@@ -352,7 +361,7 @@ def main():
             "gpu_launches": launches,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_eff / 1e12, "unit": "TFLOP/s",
                          "frac": achieved / peak_eff if peak_eff == peak_eff else None, "traffic": None,
-                         "kernel": "ipm_kernel", "flops_f32": f32, "flops_f64": f64,
+                         "kernel": "warp_ipm_kernel<float>", "flops_f32": f32, "flops_f64": f64,
                          "peak_note": "FP32 152 SMs x 128 lanes x 2 x 2.07 GHz = 80.5 TF; FP64 nominal 1.25 TF; "
                                       "peak = flop-mix-weighted"},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(b.sizes.in_bytes),

@@ -183,6 +183,9 @@ int gq_ipm_arg_default(gq_ipm_arg* arg, int mode, int precision) {
   arg->corr_k = 2.0;
   arg->reg_prim = mixed ? 1e-9 : 0.0;
   arg->ir_steps = (mixed || mode == GQ_MODE_BALANCE) ? 3 : 0;
+  // refine to 1e-12 relative: a looser inexact-Newton tolerance (1e-4) was
+  // measured to skip refinement but raise the mass-spring iteration count
+  // from 7.0 to 10.6, a net loss
   arg->ir_tol = 1e-12;
   arg->warm_min = 1e-2;
   arg->timeout_ns = 0;

@@ -80,7 +80,7 @@ __host__ __device__ SmemPlan smem_plan(const Batch& b, const Shape& sh) {
 
 namespace {
 
-constexpr double kIrFailRatio = 1e-6;      // mixed path: IR residual ratio that triggers FP64 factors
+constexpr double kIrFailRatio = 1e-6;      // mixed path: refinement residual ratio that triggers FP64 factors
 
 using namespace dev;
 

@@ -30,7 +30,7 @@ namespace {
 using namespace dev;
 
 constexpr int LDS = 33;                 // shared-memory row stride
-constexpr double kIrFailRatio = 1e-6;   // mixed path: IR residual ratio that triggers FP64 factors
+constexpr double kIrFailRatio = 1e-6;   // mixed path: refinement residual ratio that hands the QP to FP64
 
 __device__ __forceinline__ StageData wlay(const StageDesc& s) {
   return stage_data_layout(s.nx, s.nu, s.nx1, s.nbu + s.nbx, s.ng);

@@ -117,7 +117,7 @@ def test_residual_norms_match_oracle(env):
 # ----------------------------------------------------------------------------
 # a2-a4: one Newton direction through the Riccati factorisation
 # ----------------------------------------------------------------------------
-def _newton_compare(env, qps, precision, ir_steps, tol, sigma_mu=0.37):
+def _newton_compare(env, qps, precision, ir_steps, tol, sigma_mu=0.37, ir_tol=None):
     gq, QpBatch, torch = env
     b = QpBatch(qps)
     its = []
@@ -130,6 +130,8 @@ def _newton_compare(env, qps, precision, ir_steps, tol, sigma_mu=0.37):
     b.upload_sol()
     out = torch.zeros_like(b.dev_sol)
     arg = gq.default_arg(0, precision, ir_steps=ir_steps)
+    if ir_tol is not None:
+        arg.ir_tol = ir_tol
     b.newton_step(arg, sigma_mu, out)
     torch.cuda.synchronize()
     buf = out.cpu().numpy().view(np.float64)
@@ -158,7 +160,7 @@ def test_newton_step_mixed_without_refinement_is_fp32_accurate(env):
 
 def test_newton_step_mixed_with_refinement_matches_oracle(env):
     qps = [W.small_random_qp(1), W.mass_spring_qp(1)] + mixed_set()[:2]
-    _newton_compare(env, qps, precision=1, ir_steps=4, tol=1e-9)
+    _newton_compare(env, qps, precision=1, ir_steps=4, tol=1e-9, ir_tol=1e-12)
 
 
 # ----------------------------------------------------------------------------
