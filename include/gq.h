@@ -193,6 +193,13 @@ GQ_API int gq_set_general(gq_batch* b, int qp, int n, const double* C, int ldc, 
 GQ_API int gq_set_guess(gq_batch* b, int qp, const double* y, const double* pi,
                  const double* lam, const double* t);
 
+/* Copies all stage data of QP src_qp of batch `src` into QP dst_qp of batch
+ * `dst` (host staging buffers; identical stage sizes required, else
+ * GQ_ERR_DIMS).  Lets a server pack each request once and assemble
+ * micro-batches by copying blocks (Sec. 1: data in solver layout, filled by
+ * setters once). */
+GQ_API int gq_copy_qp(gq_batch* dst, int dst_qp, const gq_batch* src, int src_qp);
+
 /* ---- transfers (asynchronous on `stream`, a cudaStream_t; NULL = legacy) ---- */
 GQ_API int gq_upload(gq_batch* b, void* stream);       /* host_in  -> dev_in  */
 GQ_API int gq_upload_sol(gq_batch* b, void* stream);   /* host_sol -> dev_sol */

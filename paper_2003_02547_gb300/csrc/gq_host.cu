@@ -12,6 +12,7 @@
 
 #include "gq_internal.h"
 #include "gq_launch.h"
+#include "gq_batch.h"
 
 using namespace gq;
 
@@ -35,31 +36,18 @@ constexpr uint32_t kMagic = 0x67716231u;  // "gqb1"
 
 int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 
-struct SlotEntry {
-  int64_t key;    // slot id, -1 = empty
-  int64_t block;  // data offset (doubles)
-  int32_t stage;  // first stage using this slot
-  int32_t pad;
-};
-
 }  // namespace
 
-struct gq_batch {
-  uint32_t magic;
-  int32_t nqp;
-  int64_t n_stages, n_slots, hash_cap;
-  Layout L;
-  gq_sizes sizes;
-  int32_t ngmax;
-  int32_t nwarp;        // QPs run one per warp; they lead the order array
-  Shape shape_w, shape_b;
-  QpDesc* qp;
-  StageDesc* st;
-  int32_t* order;
-  int32_t* slot_stage;  // first stage of every distinct data block
-  SlotEntry* hash;
-  void *host_in, *host_sol, *dev_in, *dev_sol, *dev_ws;
-};
+namespace gq {
+int set_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+}  // namespace gq
+
 
 namespace {
 
@@ -840,5 +828,38 @@ extern "C" int gq_solve_noalloc(gq_batch* b, const gq_ipm_arg* arg, void* dev_in
   if (rc) return rc;
   cudaError_t e = launch_all(b, k, *arg, static_cast<cudaStream_t>(stream), LaunchKind::Solve, 0.0, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "noalloc solve launch");
+  return GQ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Copy the problem data of QP src_qp of batch src into QP dst_qp of batch dst
+// (host staging to host staging; both QPs must have identical stage sizes).
+// Used by the serving loop to assemble micro-batches from packed requests.
+// ---------------------------------------------------------------------------
+extern "C" int gq_copy_qp(gq_batch* dst, int dst_qp, const gq_batch* src, int src_qp) {
+  int rc = check_batch(dst);
+  if (rc) return rc;
+  rc = check_batch(src);
+  if (rc) return rc;
+  if (dst_qp < 0 || dst_qp >= dst->nqp || src_qp < 0 || src_qp >= src->nqp)
+    return fail(GQ_ERR_ARG, "copy_qp: QP index out of range");
+  if (dst->host_in == nullptr || src->host_in == nullptr) return fail(GQ_ERR_STATE, "copy_qp: host_in not attached");
+  const QpDesc& a = dst->qp[dst_qp];
+  const QpDesc& c = src->qp[src_qp];
+  if (a.N != c.N) return fail(GQ_ERR_DIMS, "copy_qp: horizons differ (%d vs %d)", a.N, c.N);
+  for (int n = 0; n <= a.N; ++n) {
+    const StageDesc& sa = dst->st[a.stage0 + n];
+    const StageDesc& sc = src->st[c.stage0 + n];
+    if (sa.nx != sc.nx || sa.nu != sc.nu || sa.nbx != sc.nbx || sa.nbu != sc.nbu || sa.ng != sc.ng)
+      return fail(GQ_ERR_DIMS, "copy_qp: stage %d sizes differ", n);
+  }
+  const char* sb = static_cast<const char*>(src->host_in) + src->L.data;
+  char* db = static_cast<char*>(dst->host_in) + dst->L.data;
+  for (int n = 0; n <= a.N; ++n) {
+    const StageDesc& sa = dst->st[a.stage0 + n];
+    const StageDesc& sc = src->st[c.stage0 + n];
+    const StageData lay = stage_data_layout(sa.nx, sa.nu, sa.nx1, sa.nbu + sa.nbx, sa.ng);
+    std::memcpy(db + 8 * sa.data, sb + 8 * sc.data, 8 * (size_t)lay.size);
+  }
   return GQ_OK;
 }

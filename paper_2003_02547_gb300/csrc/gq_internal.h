@@ -24,7 +24,8 @@ struct QpDesc {
   int32_t var0, eq0, side0;   // first batch-vector index of this QP
   int32_t nvt, neqt, nsidet;  // lengths of this QP's vectors
   int32_t nvmax, nxmax;       // largest stage sizes of this QP
-  int32_t pad0, pad1;
+  int32_t warm;               // 0: arg.warm_start applies; 1 + level: this QP's own warm-start level
+  int32_t pad1;
   double cost;                // flop estimate of one Riccati factorisation
 };
 static_assert(sizeof(QpDesc) == 56, "QpDesc layout");

@@ -799,7 +799,8 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
   const int64_t t_start = arg.timeout_ns > 0 ? globaltimer() : 0;
   // a0: start point
   {
-    const bool warm1 = arg.warm_start >= 1, warm2 = arg.warm_start >= 2;
+    const int wlev = qd.warm > 0 ? qd.warm - 1 : arg.warm_start;
+    const bool warm1 = wlev >= 1, warm2 = wlev >= 2;
     if (!warm1) {
       for (int i = C.v0 + tid; i < C.v1; i += blockDim.x) B.y[i] = 0.0;
       for (int i = C.e0 + tid; i < C.e1; i += blockDim.x) B.pi[i] = 0.0;

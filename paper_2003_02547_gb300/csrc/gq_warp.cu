@@ -746,7 +746,8 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
   // ---------------- full IPM (Sec. 4.2) ----------------
   const int64_t t_start = arg.timeout_ns > 0 ? globaltimer() : 0;
   if (!resume) {
-    const bool warm1 = arg.warm_start >= 1, warm2 = arg.warm_start >= 2;
+    const int wlev = qd.warm > 0 ? qd.warm - 1 : arg.warm_start;
+    const bool warm1 = wlev >= 1, warm2 = wlev >= 2;
     if (!warm1) {
       for (int i = C.v0 + lane; i < C.v1; i += 32) B.y[i] = 0.0;
       for (int i = C.e0 + lane; i < C.e1; i += 32) B.pi[i] = 0.0;

@@ -48,7 +48,31 @@ class Sizes(ctypes.Structure):
                 ("nx_max", ctypes.c_int32)]
 
 
-# name -> (restype, argtypes); the same names and order as include/gq.h
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_wait_us", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("cache_bytes", c_size_t), ("arg", IpmArg)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("src", c_void_p), ("src_qp", ctypes.c_int32), ("warm", ctypes.c_int32),
+                ("key", ctypes.c_uint64), ("t_arrival_ns", c_int64),
+                ("y", P_double), ("pi", P_double), ("lam", P_double), ("t", P_double)]
+
+
+class TicketInfo(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int32), ("code", ctypes.c_int32), ("warm_used", ctypes.c_int32),
+                ("batch_size", ctypes.c_int32), ("latency_ns", c_int64), ("wait_ns", c_int64),
+                ("stats", Stats)]
+
+
+class ServerReport(ctypes.Structure):
+    _fields_ = [(n, c_int64) for n in ("submitted", "completed", "rejected", "failed", "batches", "batched_qps",
+                                       "warm_hits", "warm_misses", "cache_entries", "cache_evictions",
+                                       "cache_skips", "deferrals", "max_lanes_busy", "max_queue")]
+
+
+# name -> (restype, argtypes); the same names and order as include/gq.h and
+# include/gq_server.h
 SIGNATURES = {
     "gq_ipm_arg_default": (c_int, [ctypes.POINTER(IpmArg), c_int, c_int]),
     "gq_batch_memsize": (c_size_t, [c_int, P_int, c_size_t, P_int]),
@@ -61,6 +85,7 @@ SIGNATURES = {
     "gq_set_box": (c_int, [c_void_p, c_int, c_int, P_int, P_double, P_double, P_int, P_double, P_double]),
     "gq_set_general": (c_int, [c_void_p, c_int, c_int, P_double, c_int, P_double, c_int, P_double, P_double]),
     "gq_set_guess": (c_int, [c_void_p, c_int, P_double, P_double, P_double, P_double]),
+    "gq_copy_qp": (c_int, [c_void_p, c_int, c_void_p, c_int]),
     "gq_upload": (c_int, [c_void_p, c_void_p]),
     "gq_upload_sol": (c_int, [c_void_p, c_void_p]),
     "gq_download": (c_int, [c_void_p, c_void_p]),
@@ -72,6 +97,14 @@ SIGNATURES = {
     "gq_get_stats": (c_int, [c_void_p, c_int, ctypes.POINTER(Stats)]),
     "gq_get_sol_offsets": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64)]),
     "gq_last_error": (ctypes.c_char_p, []),
+    "gq_server_cfg_default": (c_int, [ctypes.POINTER(ServerCfg)]),
+    "gq_server_create": (c_int, [ctypes.POINTER(ServerCfg), c_void_p, c_size_t, c_void_p, c_size_t,
+                                 ctypes.POINTER(c_void_p)]),
+    "gq_server_submit": (c_int, [c_void_p, ctypes.POINTER(Request), ctypes.POINTER(c_int64)]),
+    "gq_server_poll": (c_int, [c_void_p, c_int64, ctypes.POINTER(TicketInfo)]),
+    "gq_server_drain": (c_int, [c_void_p, c_int64]),
+    "gq_server_report_get": (c_int, [c_void_p, ctypes.POINTER(ServerReport)]),
+    "gq_server_destroy": (c_int, [c_void_p]),
 }
 
 _lib = None

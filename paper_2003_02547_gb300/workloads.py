@@ -345,6 +345,7 @@ def serving_arrivals(rate: float = 20000.0, duration: float = 1.0, repeat_frac: 
     out: List[Arrival] = []
     keys: List[int] = []
     base: dict = {}
+    pool: dict = {}
     nxt = 0
     while True:
         t += rng.exponential(1.0 / rate)
@@ -359,7 +360,10 @@ def serving_arrivals(rate: float = 20000.0, duration: float = 1.0, repeat_frac: 
         else:
             key = nxt
             nxt += 1
-            qp = ragged_random_qp(key % seed_pool, cfg=2)
+            idx = key % seed_pool
+            if idx not in pool:
+                pool[idx] = ragged_random_qp(idx, cfg=2)
+            qp = pool[idx]
             base[key] = qp
             keys.append(key)
             out.append(Arrival(t, key, qp, False))
@@ -382,5 +386,7 @@ def perturb_x0(qp: OcpQp, x0_new: np.ndarray) -> OcpQp:
         new.ug[0] = qp.ug[0] - qp.C0_full @ dx
         new.lg[0] = qp.lg[0] - qp.C0_full @ dx
     new.x0 = np.array(x0_new, dtype=np.float64)
-    new.stage_key = [(qp.name + "_w", 0)] + list(qp.stage_key[1:])
+    # stage 0 is new data: a key of its own, so that several perturbations of
+    # one QP never alias in a shared-block batch
+    new.stage_key = [(qp.name, "x0", np.asarray(x0_new, dtype=np.float64).tobytes())] + list(qp.stage_key[1:])
     return new

@@ -20,8 +20,13 @@ def gqmod():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "gq.h")).read()
-    return sorted(set(re.findall(r"GQ_API\s+[\w\s\*]+?\b(gq_\w+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            names |= set(re.findall(r"GQ_API\s+[\w\s\*]+?\b(gq_\w+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
@@ -44,6 +49,10 @@ def test_binding_names_match_header(gqmod):
 def test_struct_sizes_match_header(gqmod):
     assert ctypes.sizeof(gqmod.IpmArg) == 8 * 4 + 12 * 8 + 8
     assert ctypes.sizeof(gqmod.Stats) == 64
+    assert ctypes.sizeof(gqmod.ServerCfg) == 4 * 4 + 8 + ctypes.sizeof(gqmod.IpmArg)
+    assert ctypes.sizeof(gqmod.Request) == 8 + 4 + 4 + 8 + 8 + 4 * 8
+    assert ctypes.sizeof(gqmod.TicketInfo) == 4 * 4 + 2 * 8 + 64
+    assert ctypes.sizeof(gqmod.ServerReport) == 14 * 8
 
 
 def test_arg_defaults(gqmod):
@@ -170,3 +179,28 @@ def test_guess_and_offsets_roundtrip_on_host(gqmod):
     yy, pp, ll, tt = b.solution(1)
     np.testing.assert_array_equal(yy, y)
     np.testing.assert_array_equal(ll, lam)
+
+
+def test_server_create_validates_before_any_cuda_call(gqmod):
+    lib = gqmod.load()
+    cfg = gqmod.ServerCfg()
+    assert lib.gq_server_cfg_default(ctypes.byref(cfg)) == 0
+    assert cfg.lanes == 4 and cfg.max_batch == 256 and cfg.arg.precision == gqmod.PREC_MIXED
+    out = ctypes.c_void_p()
+    buf = np.zeros(1 << 16, dtype=np.uint8)
+    base = buf.ctypes.data + ((-buf.ctypes.data) % 256)
+    assert lib.gq_server_create(None, base, 4096, base, 4096, ctypes.byref(out)) == gqmod.GQ_ERR_ARG
+    bad = gqmod.ServerCfg()
+    lib.gq_server_cfg_default(ctypes.byref(bad))
+    bad.lanes = 0
+    assert lib.gq_server_create(ctypes.byref(bad), base, 4096, base, 4096, ctypes.byref(out)) == gqmod.GQ_ERR_ARG
+    assert "lanes" in lib.gq_last_error().decode()
+    bad.lanes = 2
+    assert lib.gq_server_create(ctypes.byref(bad), base + 8, 4096, base, 4096, ctypes.byref(out)) == gqmod.GQ_ERR_ARG
+    bad.cache_bytes = 1 << 20  # cache larger than the arena
+    assert lib.gq_server_create(ctypes.byref(bad), base, 4096, base, 4096, ctypes.byref(out)) == gqmod.GQ_ERR_SIZE
+    assert out.value is None
+    info = gqmod.TicketInfo()
+    assert lib.gq_server_poll(None, 0, ctypes.byref(info)) == gqmod.GQ_ERR_ARG
+    assert lib.gq_server_submit(None, None, None) == gqmod.GQ_ERR_ARG
+    assert lib.gq_server_destroy(None) == gqmod.GQ_ERR_ARG
