@@ -43,6 +43,10 @@ def parse():
                    help="QPs solved one launch each for the plain FP64 GPU baseline")
     p.add_argument("--cpu-sample", type=int, default=48, help="QPs in the oracle CPU baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the serving run and the ragged / large-stage batch measurements")
+    p.add_argument("--serving-rate", type=float, default=20000.0, help="offered load of the serving run (QP/s)")
+    p.add_argument("--serving-duration", type=float, default=0.5, help="seconds of Poisson arrivals")
     return p.parse_args()
 
 
@@ -175,6 +179,85 @@ def launches_per_solve(qps, arg) -> int:
     warp = any(max(q.nx[n] + q.nu[n] for n in range(q.N + 1)) <= 32 and max(q.nx) <= 32 for q in qps)
     block = any(not (max(q.nx[n] + q.nu[n] for n in range(q.N + 1)) <= 32 and max(q.nx) <= 32) for q in qps)
     return (3 if arg.fp64_fallback else 2) * warp + block
+
+
+# ----------------------------------------------------------------------------
+# serving: open-loop Poisson arrivals through the continuous-batching server
+# ----------------------------------------------------------------------------
+def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: int = 4, max_batch: int = 512):
+    """Arrivals drawn like the ragged workload (30 % repeats of an earlier key
+    with x0 + N(0, 0.01^2), warm-started from the resident iterate), every
+    request packed on the host before its arrival time, submitted at its
+    scheduled time; latency = scheduled arrival -> solution in host memory."""
+    import numpy as np
+    from paper_2003_02547_gb300 import server as S, workloads as W
+    from paper_2003_02547_gb300.batch import QpBatch
+    arr = W.serving_arrivals(rate=rate, duration=duration, seed_pool=256)
+    src = QpBatch([x.qp for x in arr], device=None)
+    budget = int(budget_gb * (1 << 30))
+    with S.Server(budget, lanes=lanes, max_batch=max_batch, cache_bytes=budget // 8,
+                  pinned_bytes=2 << 30) as srv:
+        t0 = S.now_ns() + 5_000_000
+        tickets = []
+        for i, x in enumerate(arr):
+            due = t0 + int(x.t * 1e9)
+            while S.now_ns() < due:
+                pass
+            tickets.append(srv.submit(src, i, key=x.key + 1, warm=x.warm, t_arrival_ns=due))
+        srv.drain(600.0)
+        t_end = S.now_ns()
+        rep = srv.report()
+        infos = [srv.result(t)[0] for t in tickets]
+    lat = np.array([inf.latency_ns for inf in infos], dtype=np.float64) * 1e-6
+    wait = np.array([inf.wait_ns for inf in infos], dtype=np.float64) * 1e-6
+    ok = np.array([inf.code == 0 and inf.stats.status == 0 for inf in infos])
+    warm = np.array([bool(inf.warm_used) for inf in infos])
+    iters = np.array([inf.stats.iters for inf in infos])
+    done_last = max(float(arr[i].t) * 1e3 + lat[i] for i in range(len(arr)))
+    return {
+        "offered_qps": rate, "arrival_s": duration, "requests": len(arr),
+        "throughput_qps": len(arr) / (done_last * 1e-3), "p50_ms": float(np.percentile(lat, 50)),
+        "p99_ms": float(np.percentile(lat, 99)), "admission_wait_share": float(wait.sum() / lat.sum()),
+        "converged": int(ok.sum()), "warm_started": int(warm.sum()),
+        "iters_warm_mean": float(iters[warm].mean()) if warm.any() else None,
+        "iters_cold_mean": float(iters[~warm].mean()),
+        "iters_warm_hist": np.bincount(iters[warm], minlength=1).tolist() if warm.any() else [],
+        "iters_cold_hist": np.bincount(iters[~warm], minlength=1).tolist(),
+        "batches": rep["batches"], "mean_batch": rep["batched_qps"] / max(1, rep["batches"]),
+        "max_lanes_busy": rep["max_lanes_busy"], "max_queue": rep["max_queue"],
+        "budget_gb": budget_gb, "lanes": lanes, "max_batch": max_batch,
+        "wall_s": (t_end - t0) * 1e-9,
+    }
+
+
+def batch_run(qps, dev, precision: int, reps: int = 2):
+    """Device-timed solves of one batch in one call (inputs resident)."""
+    import numpy as np
+    import torch
+    from paper_2003_02547_gb300 import gq
+    from paper_2003_02547_gb300.batch import QpBatch
+    b = QpBatch(qps, device=dev)
+    arg = gq.default_arg(gq.MODE_SPEED, precision)
+    b.upload()
+    b.solve(arg)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.solve(arg)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    b.download()
+    torch.cuda.synchronize()
+    st = b.all_stats()
+    out = {"value": len(qps) / (min(ms) * 1e-3), "unit": UNIT, "ms": min(ms), "qps": len(qps),
+           "converged": int(np.sum(st["status"] == 0)), "iters_mean": float(np.mean(st["iters"])),
+           "fp64_fallback_qps": int(np.sum(st["flags"] & gq.FLAG_FP64_FALLBACK != 0))}
+    del b
+    torch.cuda.empty_cache()
+    return out
 
 
 def dist_env():
@@ -347,6 +430,19 @@ def main():
              "p50_ms": float(np.percentile(plain_ms, 50)), "p99_ms": float(np.percentile(plain_ms, 99)),
              "sample": f"{a.plain_sample} QPs, one launch each, FP64 Riccati", "converged": plain_ok}
 
+    extras = {}
+    if rank == 0 and world == 1 and not a.no_extras:
+        del singles
+        ragged = W.ragged_batch(4096)
+        extras["ragged_4096_mixed"] = batch_run(ragged, dev, gq.PREC_MIXED)
+        extras["ragged_4096_fp64"] = batch_run(ragged, dev, gq.PREC_FP64)
+        del ragged
+        large = W.large_stage_batch(256)
+        extras["large_stage_256_mixed"] = batch_run(large, dev, gq.PREC_MIXED, reps=1)
+        extras["large_stage_256_fp64"] = batch_run(large, dev, gq.PREC_FP64, reps=1)
+        del large
+        extras["serving"] = serving_run(a.serving_rate, a.serving_duration)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -373,6 +469,7 @@ def main():
             "clocks": ck,
             "cpu_baseline": cpu,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -331,6 +331,15 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
     }
   }
 
+  // the block kernel keeps its stage matrices in shared memory unless the
+  // largest stage makes that impossible; then each block QP gets a slice of
+  // a global scratch region (read through L1/L2)
+  if (nqp > nw) {
+    Batch probe{};
+    if (ipm_smem_bytes(probe, b->shape_b) > kMaxSmem) b->shape_b.mat_global = 1;
+  }
+  const int64_t matg_elems = b->shape_b.mat_global ? (int64_t)(nqp - nw) * block_mat_elems(b->shape_b) : 0;
+
   Layout& L = b->L;
   int64_t o = 0;
   L.qpdesc = o;
@@ -370,6 +379,8 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
   o = align_up(o + fac * 8, 256);
   L.data32 = o;
   o = align_up(o + data * 4, 256);
+  L.matg = o;
+  o = align_up(o + matg_elems * 8, 256);
   L.ws_bytes = o;
 
   gq_sizes& z = b->sizes;
@@ -627,6 +638,7 @@ static int make_kernel_batch(gq_batch* b, Batch* k) {
                          L.rg2, L.rb2, L.dy2, L.dpi2, L.dlam2, L.dt2, L.tinv};
   for (int i = 0; i < 17; ++i) *w[i] = reinterpret_cast<double*>(ws + off[i]);
   k->fac = ws + L.fac;
+  k->matg = reinterpret_cast<double*>(ws + L.matg);
   if (b->nwarp < b->nqp) {
     const size_t smem = ipm_smem_bytes(*k, b->shape_b);
     if (smem > kMaxSmem)

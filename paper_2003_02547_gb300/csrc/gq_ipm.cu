@@ -58,10 +58,7 @@ __host__ __device__ SmemPlan smem_plan(const Batch& b, const Shape& sh) {
   p.red = take(32 * sizeof(double), 16);
   p.chunk = take((size_t)((sh.nside_max + 31) / 32 + 1) * sizeof(double), 16);
   p.vec = take((size_t)8 * p.vmax * sizeof(double), 16);
-  const int wide = sh.nxmax > sh.ne_max ? sh.nxmax : sh.ne_max;
-  p.mat = take(((size_t)sh.nxmax * sh.nxmax + (size_t)sh.nvmax * sh.nvmax + (size_t)sh.nvmax * (wide > 0 ? wide : 1)) *
-                   sizeof(double),
-               16);
+  p.mat = sh.mat_global ? 0 : take((size_t)block_mat_elems(sh) * sizeof(double), 16);
   p.stages = take((size_t)sh.nst_max * sizeof(StageDesc), 16);
   // ring: two buffers of (data block + FP64-sized factor block)
   p.ring_fac = (size_t)((sh.data_max * 8 + 127) / 128 * 128);
@@ -81,6 +78,7 @@ __host__ __device__ SmemPlan smem_plan(const Batch& b, const Shape& sh) {
 namespace {
 
 constexpr double kIrFailRatio = 1e-6;      // mixed path: refinement residual ratio that triggers FP64 factors
+constexpr double kInexact = 0.1;           // mixed path: direction residual allowed per unit of iterate residual
 
 using namespace dev;
 
@@ -88,7 +86,7 @@ using namespace dev;
 // block-wide reductions (max/min are exact, so their order does not matter)
 // ---------------------------------------------------------------------------
 struct OpMax {
-  __device__ double operator()(double a, double b) const { return fmax(a, b); }
+  __device__ double operator()(double a, double b) const { return max_nan(a, b); }
 };
 struct OpMin {
   __device__ double operator()(double a, double b) const { return fmin(a, b); }
@@ -175,7 +173,7 @@ __device__ __forceinline__ int elim_size(const StageDesc& s, int n) { return n =
 
 template <typename Tf>
 __device__ __forceinline__ Tf* fac_global(const Batch& B, const StageDesc& s) {
-  return static_cast<Tf*>(B.fac) + s.fac;
+  return reinterpret_cast<Tf*>(static_cast<double*>(B.fac) + s.fac);
 }
 
 // value of constraint c of stage s at the stage vector y (length nv)
@@ -203,7 +201,7 @@ __device__ __forceinline__ void ring_issue(Ctx& C, int n, int b, int fac_elem) {
     mbar_arrive_expect_tx(&C.ring.bar[b], dbytes + fbytes);
     bulk_g2s(C.ring.buf[b], B.data + s.data, dbytes, &C.ring.bar[b]);
     if (fbytes)
-      bulk_g2s(C.ring.buf[b] + C.ring.fac_off, static_cast<const unsigned char*>(B.fac) + s.fac * fac_elem, fbytes,
+      bulk_g2s(C.ring.buf[b] + C.ring.fac_off, static_cast<const unsigned char*>(B.fac) + s.fac * 8, fbytes,
                &C.ring.bar[b]);
   }
 }
@@ -227,7 +225,7 @@ __device__ void sweep(Ctx& C, bool backward, int fac_elem, F f) {
     for (int k = 0; k <= N; ++k) {
       const int n = backward ? N - k : k;
       const StageDesc& s = C.st[n];
-      const unsigned char* fac = static_cast<const unsigned char*>(B.fac) + s.fac * (fac_elem ? fac_elem : 1);
+      const unsigned char* fac = static_cast<const unsigned char*>(B.fac) + s.fac * 8;
       f(n, B.data + s.data, static_cast<const void*>(fac));
       __syncthreads();
     }
@@ -279,7 +277,7 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
       if (c >= 0) acc -= lm[c] - lm[nc + c];
     }
     og[s.var + i] = acc;
-    mx.g = fmax(mx.g, fabs(acc));
+    mx.g = max_nan(mx.g, fabs(acc));
   }
   if (n < C.N) {
     const double* yn1 = y + C.st[n + 1].var + C.st[n + 1].nu;
@@ -288,7 +286,7 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
       for (int i = 0; i < nv; ++i) acc = fma(D[L.BAt + (int64_t)i * L.ldb + k], yn[i], acc);
       acc -= yn1[k];
       ob[s.eq + k] = acc;
-      mx.b = fmax(mx.b, fabs(acc));
+      mx.b = max_nan(mx.b, fabs(acc));
     }
   }
   if (rd != nullptr) {
@@ -301,7 +299,7 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
       if (hi != INFINITY) b = v - hi + t[iu];
       rd[il] = a;
       rd[iu] = b;
-      mx.d = fmax(mx.d, fmax(fabs(a), fabs(b)));
+      mx.d = max_nan(mx.d, max_nan(fabs(a), fabs(b)));
     }
   }
 }
@@ -513,7 +511,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
         for (int gg = 0; gg < s.ng; ++gg) gi = fma(-D[L.DC + (int64_t)gg * nv + i], vs[nb + gg], gi);
         if (nb > 0 && bmap[i] >= 0) gi -= vs[bmap[i]];
       }
-      scale = fmax(scale, fabs(gi));
+      scale = max_nan(scale, fabs(gi));
       Tf acc = (Tf)gi;
       if (n < C.N) {
         const double* ba = D + L.BAt + (int64_t)i * L.ldb;
@@ -522,7 +520,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
       phi[i] = acc;
     }
     if (n < C.N)
-      for (int k = tid; k < nx1; k += NT) scale = fmax(scale, fabs(rb[s.eq + k]));
+      for (int k = tid; k < nx1; k += NT) scale = max_nan(scale, fabs(rb[s.eq + k]));
     __syncthreads();
     // l = X phi_e
     for (int i = tid; i < ne; i += NT) {
@@ -657,6 +655,7 @@ struct Dir {
 // work counters reported in gq_stats (thread-uniform values)
 struct Count {
   int ir = 0, fact = 0, fact64 = 0, solve = 0, res = 0;
+  double m = 0.0;  // residual of the last refined direction (r_g, r_b rows)
 };
 
 // Newton direction of eq. (delta) for the current r_m with the factors in
@@ -678,8 +677,9 @@ __device__ double newton_dir(Ctx& C, const Dir& d, int ir, double ir_tol, Count*
       stage_residual(C, n, D, d.dy, d.dpi, d.dlam, nullptr, B.rg2, B.rb2, nullptr, true, B.rg, B.rb, mx);
     });
     ++cnt->res;
-    const double m = block_reduce(fmax(mx.g, mx.b), C.red, OpMax());
+    const double m = block_reduce(max_nan(mx.g, mx.b), C.red, OpMax());
     ratio = mr > 0.0 ? m / mr : 0.0;
+    cnt->m = m;
     if (k == ir || m <= ir_tol * mr) break;
     // correction: same factors, the refinement residual as right-hand side
     riccati_solve<Tf>(C, B.rg2, nullptr, nullptr, B.rb2, B.dy2, B.dpi2, B.dlam2, B.dt2);
@@ -736,7 +736,10 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
   C.e1 = qd.eq0 + qd.neqt;
   C.vbuf = reinterpret_cast<double*>(smem + P.vec);
   C.vmax = P.vmax;
-  C.mat = smem + P.mat;
+  // stage matrices: shared memory, or this QP's slice of the global scratch
+  // when the largest stage does not fit (one slice per block of the launch)
+  C.mat = sh.mat_global ? static_cast<void*>(B.matg + (int64_t)blockIdx.x * block_mat_elems(sh))
+                        : static_cast<void*>(smem + P.mat);
   C.nvmax = sh.nvmax;
   C.nxmax = sh.nxmax;
   C.ring.buf[0] = smem + P.ring0;
@@ -903,6 +906,9 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
     else
       newton_dir<float>(C, d, 0, 0.0, &cnt);
     const int ir = (mixed && !fp64) || arg.mode == GQ_MODE_BALANCE ? arg.ir_steps : 0;
+    // a refined FP32 direction must also be an inexact-Newton step for the
+    // unscaled exit rule: its own residual well below the iterate's
+    const double inexact = kInexact * fmax(fmax(r.g, r.b), arg.tol_stat);
     if (C.nact > 0) {
       const double a_aff = fmin(1.0, max_step(C, d.dlam, d.dt));
       const double mu_aff = mu_after(C, a_aff, d.dlam, d.dt);
@@ -925,7 +931,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
                        : newton_dir<float>(C, d, ir, arg.ir_tol, &cnt);
         }
       }
-      if (!fp64 && arg.fp64_fallback && ir > 0 && !(ratio <= kIrFailRatio)) {
+      if (!fp64 && arg.fp64_fallback && ir > 0 && !(ratio <= kIrFailRatio && cnt.m <= inexact)) {
         // a7 failed to recover the accuracy of the FP32 factors: refactor in FP64
         fp64 = true;
         flags |= GQ_FLAG_FP64_FALLBACK;
@@ -937,7 +943,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
         // no inequalities: refine the single Newton step
         const double ratio = fp64 ? newton_dir<double>(C, d, ir, arg.ir_tol, &cnt)
                                   : newton_dir<float>(C, d, ir, arg.ir_tol, &cnt);
-        if (!fp64 && arg.fp64_fallback && !(ratio <= kIrFailRatio)) {
+        if (!fp64 && arg.fp64_fallback && !(ratio <= kIrFailRatio && cnt.m <= inexact)) {
           fp64 = true;
           flags |= GQ_FLAG_FP64_FALLBACK;
           continue;

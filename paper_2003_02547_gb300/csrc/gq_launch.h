@@ -21,7 +21,17 @@ struct Shape {
   int nside_max;     // largest side count of one QP
   int nvmax, nxmax, ngmax;
   int64_t data_max;  // largest stage data block (elements)
+  int32_t mat_global;  // block kernel: stage matrices in the global workspace (too large for shared memory)
+  int32_t pad;
 };
+
+// Elements (doubles) of the block kernel's stage-matrix scratch for a shape:
+// L_{n+1} (nxmax^2), Phi (nvmax^2), M or X (nvmax x max(nxmax, ne_max)).
+__host__ __device__ inline int64_t block_mat_elems(const Shape& sh) {
+  const int wide = sh.nxmax > sh.ne_max ? sh.nxmax : sh.ne_max;
+  return ((int64_t)sh.nxmax * sh.nxmax + (int64_t)sh.nvmax * sh.nvmax + (int64_t)sh.nvmax * (wide > 0 ? wide : 1) +
+          15) & ~int64_t(15);
+}
 
 // QPs whose stages all have nu + nx <= 32 and nx <= 32 run one per warp.
 constexpr int kWarpMaxNv = 32;

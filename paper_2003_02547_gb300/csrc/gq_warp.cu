@@ -31,6 +31,7 @@ using namespace dev;
 
 constexpr int LDS = 33;                 // shared-memory row stride
 constexpr double kIrFailRatio = 1e-6;   // mixed path: refinement residual ratio that hands the QP to FP64
+constexpr double kInexact = 0.1;        // mixed path: direction residual allowed per unit of iterate residual
 
 __device__ __forceinline__ StageData wlay(const StageDesc& s) {
   return stage_data_layout(s.nx, s.nu, s.nx1, s.nbu + s.nbx, s.ng);
@@ -88,7 +89,7 @@ __device__ __forceinline__ void wissue(WCtx& C, int n, int b, const unsigned cha
     fence_async_shared();
     mbar_arrive_expect_tx(&C.bar[b], dbytes + fbytes);
     bulk_g2s(C.ring[b], dbase + s.data * delem, dbytes, &C.bar[b]);
-    if (fbytes) bulk_g2s(C.ring[b] + C.fac_off, fbase + s.fac * felem, fbytes, &C.bar[b]);
+    if (fbytes) bulk_g2s(C.ring[b] + C.fac_off, fbase + s.fac * 8, fbytes, &C.bar[b]);
   }
 }
 
@@ -172,7 +173,7 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
         if (c >= 0) acc -= lm[c] - lm[nc + c];
       }
       og[s.var + lane] = acc;
-      mx.g = fmax(mx.g, fabs(acc));
+      mx.g = max_nan(mx.g, fabs(acc));
     }
   }
   // r_b, row `lane`
@@ -191,7 +192,7 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
       const double x1 = y[C.st[n + 1].var + C.st[n + 1].nu + lane];
       const double acc = (lin ? add_b[s.eq + lane] : D[L.b + lane]) + (a0 + a1) - x1;
       ob[s.eq + lane] = acc;
-      mx.b = fmax(mx.b, fabs(acc));
+      mx.b = max_nan(mx.b, fabs(acc));
     }
   }
   // r_d per side
@@ -214,7 +215,7 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
         if (hi != INFINITY) bb = v - hi + t[iu];
         rd[il] = a;
         rd[iu] = bb;
-        mx.d = fmax(mx.d, fmax(fabs(a), fabs(bb)));
+        mx.d = max_nan(mx.d, max_nan(fabs(a), fabs(bb)));
       }
     }
     __syncwarp();
@@ -355,7 +356,7 @@ __device__ __forceinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double
   __syncwarp();
   // store the factor block (ld odd_ld(nv)): X in the leading block, L elsewhere;
   // keep L_n = L_kk in sL
-  T* F = static_cast<T*>(B.fac) + s.fac;
+  T* F = reinterpret_cast<T*>(static_cast<double*>(B.fac) + s.fac);
   const int ldf = odd_ld(nv);
   for (int r = 0; r < nv; ++r) {
     if (act) {
@@ -428,12 +429,12 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
         for (int gg = 0; gg < s.ng; ++gg) gi = fma(-(double)D[L.DC + (int64_t)gg * nv + lane], C.sv[nb + gg], gi);
         if (nb > 0 && bmap[lane] >= 0) gi -= C.sv[bmap[lane]];
       }
-      scale = fmax(scale, fabs(gi));
+      scale = max_nan(scale, fabs(gi));
     }
     T vb = T(0);
     if (n < C.N) {
       const double rbd = lane < nx1 ? rb[s.eq + lane] : 0.0;
-      scale = fmax(scale, fabs(rbd));
+      scale = max_nan(scale, fabs(rbd));
       const T rbl = (T)rbd;
       // va = L_{n+1}' rb
       T va = T(0);
@@ -594,6 +595,7 @@ struct WDir {
 };
 struct WCount {
   int ir = 0, fact = 0, fact64 = 0, solve = 0, res = 0;
+  double m = 0.0;  // residual of the last refined direction (r_g, r_b rows)
 };
 
 template <typename T>
@@ -610,8 +612,9 @@ __device__ double wnewton(WCtx& C, const WDir& d, int ir, double ir_tol, WCount*
                  B.rg, B.rb, mx);
     });
     ++cnt->res;
-    const double m = warp_max(fmax(mx.g, mx.b));
+    const double m = warp_max(max_nan(mx.g, mx.b));
     ratio = mr > 0.0 ? m / mr : 0.0;
+    cnt->m = m;
     if (k == ir || m <= ir_tol * mr) break;
     wsolve<T>(C, B.rg2, nullptr, nullptr, B.rb2, B.dy2, B.dpi2, B.dlam2, B.dt2);
     for (int i = C.v0 + C.lane; i < C.v1; i += 32) d.dy[i] += B.dy2[i];
@@ -867,6 +870,9 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
     }
     wnewton<T>(C, d, 0, 0.0, &cnt);
     const int ir = (mixed && !fp64) || arg.mode == GQ_MODE_BALANCE ? arg.ir_steps : 0;
+    // a refined FP32 direction must also be an inexact-Newton step for the
+    // unscaled exit rule: its own residual well below the iterate's
+    const double inexact = kInexact * fmax(fmax(r.g, r.b), arg.tol_stat);
     if (C.nact > 0) {
       const double a_aff = fmin(1.0, wmax_step(C, d.dlam, d.dt));
       const double mu_aff = wmu_after(C, a_aff, d.dlam, d.dt);
@@ -886,7 +892,7 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
           ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
         }
       }
-      if (!fp64 && arg.fp64_fallback && ir > 0 && !(ratio <= kIrFailRatio)) {
+      if (!fp64 && arg.fp64_fallback && ir > 0 && !(ratio <= kIrFailRatio && cnt.m <= inexact)) {
         // refinement could not recover the FP32 factors' accuracy: the FP64
         // launch continues this QP from the current iterate
         status = kStatusResumeFp64;
@@ -896,7 +902,7 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
     } else {
       if (ir > 0) {
         const double ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
-        if (!fp64 && arg.fp64_fallback && !(ratio <= kIrFailRatio)) {
+        if (!fp64 && arg.fp64_fallback && !(ratio <= kIrFailRatio && cnt.m <= inexact)) {
           status = kStatusResumeFp64;
           break;
         }

@@ -245,6 +245,28 @@ def test_batch_invariance_bitwise(env):
         assert alone.all_stats()["iters"][0] == inmix.all_stats()["iters"][4]
 
 
+def test_stale_workspace_and_solution_buffers_do_not_matter(env):
+    """A cold solve reads nothing it did not write: the same bits with zeroed
+    and with NaN-filled workspace and solution buffers (the server reuses
+    its lanes' buffers without clearing them)."""
+    gq, QpBatch, torch = env
+    qps = [W.ragged_random_qp(i) for i in range(3)] + [W.mass_spring_qp(2), W.small_random_qp(5)]
+    for prec in (0, 1):
+        arg = gq.default_arg(0, prec)
+        ref = solve_gpu(env, qps, precision=prec)
+        b = QpBatch(qps)
+        b.dev_ws.fill_(0xFF)
+        b.dev_sol.fill_(0xFF)
+        b.upload()
+        b.solve(arg)
+        b.download()
+        torch.cuda.synchronize()
+        for i in range(len(qps)):
+            for a, c in zip(ref.solution(i), b.solution(i)):
+                np.testing.assert_array_equal(a, c, err_msg=f"precision {prec}, QP {i}")
+            assert ref.all_stats()["iters"][i] == b.all_stats()["iters"][i]
+
+
 def test_status_paths_do_not_poison_neighbours(env):
     gq, QpBatch, torch = env
     good = W.small_random_qp(0)
