@@ -219,6 +219,8 @@ def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: in
         "throughput_qps": len(arr) / (done_last * 1e-3), "p50_ms": float(np.percentile(lat, 50)),
         "p99_ms": float(np.percentile(lat, 99)), "admission_wait_share": float(wait.sum() / lat.sum()),
         "converged": int(ok.sum()), "warm_started": int(warm.sum()),
+        "not_converged_status": sorted(int(inf.stats.status) for inf in infos if inf.code == 0 and inf.stats.status),
+        "rejected_or_failed": int(sum(inf.code != 0 for inf in infos)),
         "iters_warm_mean": float(iters[warm].mean()) if warm.any() else None,
         "iters_cold_mean": float(iters[~warm].mean()),
         "iters_warm_hist": np.bincount(iters[warm], minlength=1).tolist() if warm.any() else [],
@@ -442,6 +444,10 @@ def main():
         extras["large_stage_256_fp64"] = batch_run(large, dev, gq.PREC_FP64, reps=1)
         del large
         extras["serving"] = serving_run(a.serving_rate, a.serving_duration)
+        # the same request mix below the ragged batch capacity: latency
+        # without a standing queue
+        light = 0.7 * extras["ragged_4096_mixed"]["value"]
+        extras["serving_below_capacity"] = serving_run(light, max(1.0, 600.0 / light))
 
     if rank == 0:
         line = {

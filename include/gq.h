@@ -78,6 +78,11 @@ extern "C" {
 #define GQ_STATUS_TIMEOUT 4  /* arg.timeout_ns elapsed on the device          */
 /* flag bits in gq_stats.flags */
 #define GQ_FLAG_FP64_FALLBACK 1  /* mixed path switched this QP to FP64 factors */
+#define GQ_FLAG_REGULARIZED 2    /* an FP64 factorisation lost a pivot: it was
+                                    redone with a 1e-10 primal regularisation
+                                    and, if still indefinite, the iteration
+                                    was redone with lambda, t lifted to
+                                    max(1e-10, 1e-2 max(|r_g|, |r_b|))       */
 
 /* ---- solver arguments (Sec. 4.2) ---- */
 #define GQ_MODE_SPEED 0     /* delta formulation, residual-based exit (Sec. 4.2) */

@@ -38,8 +38,9 @@ def _compile(src):
 
 
 def _headers():
+    inc = os.path.join(HERE, "..", "include")
     hs = [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".h")]
-    hs.append(os.path.join(HERE, "..", "include", "gq.h"))
+    hs += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     return hs
 
 

@@ -78,6 +78,9 @@ __host__ __device__ SmemPlan smem_plan(const Batch& b, const Shape& sh) {
 namespace {
 
 constexpr double kIrFailRatio = 1e-6;      // mixed path: refinement residual ratio that triggers FP64 factors
+constexpr double kLift = 1e-10;          // smallest floor of lambda, t after a lost FP64 pivot
+constexpr double kLiftRel = 1e-2;        // ... relative to the stationarity residual
+constexpr double kRegRetry = 1e-10;        // primal regularisation of an FP64 refactorisation after a lost pivot
 constexpr double kInexact = 0.1;           // mixed path: direction residual allowed per unit of iterate residual
 
 using namespace dev;
@@ -262,14 +265,27 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
   const double* lm = lam + s.side;
   const int32_t* bmap = box_idx(D, L) + nb;
   for (int i = tid; i < nv; i += NT) {
+    // four partial sums per dot product: FP64 FMA latency dominates a
+    // single dependent chain
     const double* row = D + L.RSQ + (int64_t)i * L.ldr;
-    double acc = lin ? add_g[s.var + i] : D[L.rq + i];
-    for (int j = 0; j < nv; ++j) acc = fma(row[j], yn[j], acc);
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    int j = 0;
+    for (; j + 3 < nv; j += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = fma(row[j + u], yn[j + u], a[u]);
+    }
+    for (; j < nv; ++j) a[0] = fma(row[j], yn[j], a[0]);
     if (n < C.N) {
       const double* ba = D + L.BAt + (int64_t)i * L.ldb;
       const double* pn1 = pi + s.eq;
-      for (int k = 0; k < nx1; ++k) acc = fma(ba[k], pn1[k], acc);
+      int k = 0;
+      for (; k + 3 < nx1; k += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = fma(ba[k + u], pn1[k + u], a[u]);
+      }
+      for (; k < nx1; ++k) a[0] = fma(ba[k], pn1[k], a[0]);
     }
+    double acc = (lin ? add_g[s.var + i] : D[L.rq + i]) + ((a[0] + a[1]) + (a[2] + a[3]));
     if (n > 0 && i >= s.nu) acc -= pi[C.st[n - 1].eq + (i - s.nu)];
     for (int g = 0; g < s.ng; ++g) acc = fma(-D[L.DC + (int64_t)g * nv + i], lm[nb + g] - lm[nc + nb + g], acc);
     if (nb > 0) {
@@ -282,8 +298,14 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
   if (n < C.N) {
     const double* yn1 = y + C.st[n + 1].var + C.st[n + 1].nu;
     for (int k = tid; k < nx1; k += NT) {
-      double acc = lin ? add_b[s.eq + k] : D[L.b + k];
-      for (int i = 0; i < nv; ++i) acc = fma(D[L.BAt + (int64_t)i * L.ldb + k], yn[i], acc);
+      double a[4] = {0.0, 0.0, 0.0, 0.0};
+      int i = 0;
+      for (; i + 3 < nv; i += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = fma(D[L.BAt + (int64_t)(i + u) * L.ldb + k], yn[i + u], a[u]);
+      }
+      for (; i < nv; ++i) a[0] = fma(D[L.BAt + (int64_t)i * L.ldb + k], yn[i], a[0]);
+      double acc = (lin ? add_b[s.eq + k] : D[L.b + k]) + ((a[0] + a[1]) + (a[2] + a[3]));
       acc -= yn1[k];
       ob[s.eq + k] = acc;
       mx.b = max_nan(mx.b, fabs(acc));
@@ -330,14 +352,47 @@ __device__ Norms residuals(Ctx& C) {
 // ---------------------------------------------------------------------------
 // a3: square-root Riccati factorisation, one stage (called for n = N..0)
 // ---------------------------------------------------------------------------
+// Register micro-tiles of kT x kT outputs per thread for the stage products,
+// and a Cholesky panel width; tiles are dealt to threads round-robin, and each
+// output's sum runs in a fixed order, so the result does not depend on
+// blockDim.
+constexpr int kT = 4;
+constexpr int kPanel = 8;
+
+// Sum of f(k) for k in [k0, k1) in four interleaved partial sums (a fixed
+// order that depends on k0, k1 only): short dependent FMA chains.
+template <typename Tf, class F>
+__device__ __forceinline__ Tf dot4(int k0, int k1, F f) {
+  Tf a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  int k = k0;
+  for (; k + 3 < k1; k += 4) {
+    a0 += f(k);
+    a1 += f(k + 1);
+    a2 += f(k + 2);
+    a3 += f(k + 3);
+  }
+  for (; k < k1; ++k) a0 += f(k);
+  return (a0 + a1) + (a2 + a3);
+}
+
+// lower-triangle tile index -> (I, J), J <= I
+__device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
+  int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= t) ++i;
+  while (i * (i + 1) / 2 > t) --i;
+  I = i;
+  J = t - i * (i + 1) / 2;
+}
+
 template <typename Tf>
 __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
   const Batch& B = *C.B;
   const int tid = threadIdx.x, NT = blockDim.x;
-  Tf* sL = static_cast<Tf*>(C.mat);        // L_{n+1}: nx1 x nx1
-  Tf* sPhi = sL + C.nxmax * C.nxmax;       // nv x nv
-  Tf* sM = sPhi + C.nvmax * C.nvmax;       // nv x nx1, also X temp
-  Tf* sw = reinterpret_cast<Tf*>(C.vbuf);  // per-constraint weight, then pivots
+  const int ldP = block_ld(C.nvmax);
+  Tf* sL = static_cast<Tf*>(C.mat);        // L_{n+1}: nx1 x nx1 (ld nx1), zero above the diagonal
+  Tf* sPhi = sL + C.nxmax * C.nxmax;       // nv x nv (ld ldP)
+  Tf* sMt = sPhi + C.nvmax * ldP;          // M': nx1 x nv (ld ldP), later X
+  Tf* sw = reinterpret_cast<Tf*>(C.vbuf);  // per-constraint weight
   bool ok = true;
   const StageDesc s = C.st[n];
   const StageData L = lay(s);
@@ -353,85 +408,186 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
     if (D[L.hi + c] != INFINITY) w += lm[nc + c] / tt[nc + c];
     sw[c] = (Tf)w;
   }
-  // M = [B A]' L_{n+1}
+  const int nI = (nv + kT - 1) / kT;
+  // M' = ([B A]' L_{n+1})': Mt[j][i] = sum_{k >= j} BAt[i][k] L[k][j]
   if (n < C.N) {
-    for (int e = tid; e < nv * nx1; e += NT) {
-      const int i = e / nx1, j = e - i * nx1;
-      const double* ba = D + L.BAt + (int64_t)i * L.ldb;
-      Tf acc = 0;
-      for (int k = j; k < nx1; ++k) acc += (Tf)ba[k] * sL[k * nx1 + j];
-      sM[i * nx1 + j] = acc;
+    const int nJ = (nx1 + kT - 1) / kT;
+    for (int t = tid; t < nI * nJ; t += NT) {
+      const int I = t / nJ, J = t - I * nJ;
+      Tf acc[kT][kT] = {};
+      const double* ba[kT];
+#pragma unroll
+      for (int r = 0; r < kT; ++r) ba[r] = D + L.BAt + (int64_t)min(I * kT + r, nv - 1) * L.ldb;
+      for (int k = J * kT; k < nx1; ++k) {
+        Tf a[kT], bb[kT];
+#pragma unroll
+        for (int r = 0; r < kT; ++r) a[r] = (Tf)ba[r][k];
+#pragma unroll
+        for (int c = 0; c < kT; ++c) bb[c] = J * kT + c < nx1 ? sL[k * nx1 + J * kT + c] : (Tf)0;
+#pragma unroll
+        for (int r = 0; r < kT; ++r)
+#pragma unroll
+          for (int c = 0; c < kT; ++c) acc[r][c] += a[r] * bb[c];
+      }
+#pragma unroll
+      for (int c = 0; c < kT; ++c) {
+        const int j = J * kT + c;
+        if (j < nx1) {
+#pragma unroll
+          for (int r = 0; r < kT; ++r)
+            if (I * kT + r < nv) sMt[j * ldP + I * kT + r] = acc[r][c];
+        }
+      }
     }
   }
   __syncthreads();
-  // Phi = RSQ + reg I + W_box + [D C]' diag(w_g) [D C] + M M'   (lower triangle)
-  for (int e = tid; e < nv * nv; e += NT) {
-    const int i = e / nv, j = e - i * nv;
-    if (j > i) continue;
-    Tf acc = (Tf)D[L.RSQ + (int64_t)i * L.ldr + j];
-    if (i == j) {
-      acc += (Tf)reg;
-      if (nb > 0 && bmap[i] >= 0) acc += sw[bmap[i]];
+  // Phi = RSQ + reg I + W_box + [D C]' diag(w_g) [D C] + M M'   (lower tiles)
+  for (int t = tid; t < nI * (nI + 1) / 2; t += NT) {
+    int I, J;
+    tri_tile(t, I, J);
+    Tf acc[kT][kT];
+#pragma unroll
+    for (int r = 0; r < kT; ++r) {
+      const int i = min(I * kT + r, nv - 1);
+#pragma unroll
+      for (int c = 0; c < kT; ++c) {
+        const int j = min(J * kT + c, nv - 1);
+        const int hi = i > j ? i : j, lo = i > j ? j : i;
+        acc[r][c] = (Tf)D[L.RSQ + (int64_t)hi * L.ldr + lo];
+      }
     }
-    for (int g = 0; g < s.ng; ++g)
-      acc += (Tf)D[L.DC + (int64_t)g * nv + i] * sw[nb + g] * (Tf)D[L.DC + (int64_t)g * nv + j];
-    if (n < C.N)
-      for (int k = 0; k < nx1; ++k) acc += sM[i * nx1 + k] * sM[j * nx1 + k];
-    sPhi[i * nv + j] = acc;
+    for (int g = 0; g < s.ng; ++g) {
+      const double* row = D + L.DC + (int64_t)g * nv;
+      const Tf wg = sw[nb + g];
+      Tf a[kT], bb[kT];
+#pragma unroll
+      for (int r = 0; r < kT; ++r) a[r] = (Tf)row[min(I * kT + r, nv - 1)] * wg;
+#pragma unroll
+      for (int c = 0; c < kT; ++c) bb[c] = (Tf)row[min(J * kT + c, nv - 1)];
+#pragma unroll
+      for (int r = 0; r < kT; ++r)
+#pragma unroll
+        for (int c = 0; c < kT; ++c) acc[r][c] += a[r] * bb[c];
+    }
+    if (n < C.N) {
+      for (int k = 0; k < nx1; ++k) {
+        const Tf* mk = sMt + k * ldP;
+        Tf a[kT], bb[kT];
+#pragma unroll
+        for (int r = 0; r < kT; ++r) a[r] = mk[min(I * kT + r, nv - 1)];
+#pragma unroll
+        for (int c = 0; c < kT; ++c) bb[c] = mk[min(J * kT + c, nv - 1)];
+#pragma unroll
+        for (int r = 0; r < kT; ++r)
+#pragma unroll
+          for (int c = 0; c < kT; ++c) acc[r][c] += a[r] * bb[c];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kT; ++r) {
+      const int i = I * kT + r;
+#pragma unroll
+      for (int c = 0; c < kT; ++c) {
+        const int j = J * kT + c;
+        if (i < nv && j <= i) {
+          Tf v = acc[r][c];
+          if (i == j) {
+            v += (Tf)reg;
+            if (nb > 0 && bmap[i] >= 0) v += sw[bmap[i]];
+          }
+          sPhi[i * ldP + j] = v;
+        }
+      }
+    }
   }
   __syncthreads();
-  // right-looking Cholesky, outer-product form on the unscaled columns
-  for (int k = 0; k < nv; ++k) {
-    Tf d = sPhi[k * nv + k];
-    if (!(d > (Tf)0)) {
-      ok = false;
-      d = (Tf)1;
-    }
-    const Tf inv = (Tf)1 / d;
-    for (int i = k + 1 + tid; i < nv; i += NT) {
-      const Tf lik = sPhi[i * nv + k] * inv;
-      Tf* ri = sPhi + i * nv;
-      for (int j = k + 1; j <= i; ++j) ri[j] -= lik * sPhi[j * nv + k];
+  // blocked right-looking Cholesky: one warp factors each kPanel-wide column
+  // panel, then all threads apply its rank-kPanel update to the trailing
+  // lower triangle
+  const int lane = tid & 31;
+  for (int p0 = 0; p0 < nv; p0 += kPanel) {
+    const int pw = min(kPanel, nv - p0);
+    if (tid < 32) {
+      for (int c = 0; c < pw; ++c) {
+        const int col = p0 + c;
+        Tf d = sPhi[col * ldP + col];
+        if (!(d > (Tf)0)) {
+          ok = false;
+          d = (Tf)1;
+        }
+        const Tf lcc = sqrt(d);
+        const Tf inv = (Tf)1 / lcc;
+        for (int r = col + 1 + lane; r < nv; r += 32) sPhi[r * ldP + col] *= inv;
+        __syncwarp();
+        if (lane == 0) sPhi[col * ldP + col] = lcc;
+        for (int r = col + 1 + lane; r < nv; r += 32) {
+          const Tf lr = sPhi[r * ldP + col];
+          const int cend = min(p0 + pw - 1, r);
+          for (int c2 = col + 1; c2 <= cend; ++c2) sPhi[r * ldP + c2] -= lr * sPhi[c2 * ldP + col];
+        }
+        __syncwarp();
+      }
     }
     __syncthreads();
+    const int q0 = p0 + pw, m = nv - q0;
+    if (m > 0) {
+      const int nQ = (m + kT - 1) / kT;
+      for (int t = tid; t < nQ * (nQ + 1) / 2; t += NT) {
+        int I, J;
+        tri_tile(t, I, J);
+        Tf acc[kT][kT] = {};
+        const Tf* ri[kT];
+        const Tf* rj[kT];
+#pragma unroll
+        for (int r = 0; r < kT; ++r) {
+          ri[r] = sPhi + min(q0 + I * kT + r, nv - 1) * ldP + p0;
+          rj[r] = sPhi + min(q0 + J * kT + r, nv - 1) * ldP + p0;
+        }
+        for (int c = 0; c < pw; ++c) {
+          Tf a[kT], bb[kT];
+#pragma unroll
+          for (int r = 0; r < kT; ++r) {
+            a[r] = ri[r][c];
+            bb[r] = rj[r][c];
+          }
+#pragma unroll
+          for (int r = 0; r < kT; ++r)
+#pragma unroll
+            for (int c2 = 0; c2 < kT; ++c2) acc[r][c2] += a[r] * bb[c2];
+        }
+#pragma unroll
+        for (int r = 0; r < kT; ++r) {
+          const int i = q0 + I * kT + r;
+#pragma unroll
+          for (int c2 = 0; c2 < kT; ++c2) {
+            const int j = q0 + J * kT + c2;
+            if (i < nv && j <= i) sPhi[i * ldP + j] -= acc[r][c2];
+          }
+        }
+      }
+      __syncthreads();
+    }
   }
-  // scale columns: L_jj = sqrt(d_j), L_ij = Phi_ij / sqrt(d_j)
-  Tf* sdiag = sw;  // weights no longer needed
-  for (int j = tid; j < nv; j += NT) {
-    const Tf d = sPhi[j * nv + j];
-    sdiag[j] = d > (Tf)0 ? sqrt(d) : (Tf)1;
-  }
-  __syncthreads();
-  for (int e = tid; e < nv * nv; e += NT) {
-    const int i = e / nv, j = e - i * nv;
-    if (j > i) continue;
-    sPhi[i * nv + j] = (i == j) ? sdiag[j] : sPhi[i * nv + j] / sdiag[j];
-  }
-  __syncthreads();
-  // X = L_ee^{-1} (lower), column j by thread j, into the M buffer
+  ok = __syncthreads_and(ok) != 0;
+  // X = L_ee^{-1} (lower), column j by thread j, into the M' buffer (ld ne)
   for (int j = tid; j < ne; j += NT) {
-    sM[j * ne + j] = (Tf)1 / sPhi[j * nv + j];
+    sMt[j * ne + j] = (Tf)1 / sPhi[j * ldP + j];
     for (int i = j + 1; i < ne; ++i) {
       Tf acc = 0;
-      for (int k = j; k < i; ++k) acc += sPhi[i * nv + k] * sM[k * ne + j];
-      sM[i * ne + j] = -acc / sPhi[i * nv + i];
+      for (int k = j; k < i; ++k) acc += sPhi[i * ldP + k] * sMt[k * ne + j];
+      sMt[i * ne + j] = -acc / sPhi[i * ldP + i];
     }
   }
   __syncthreads();
-  for (int e = tid; e < ne * ne; e += NT) {
-    const int i = e / ne, j = e - i * ne;
-    if (j <= i) sPhi[i * nv + j] = sM[i * ne + j];
-  }
-  __syncthreads();
-  // store the factor, keep L_n = L_kk for stage n-1
+  // store the factor (ld nv), X in place of L_ee; keep L_n = L_kk for stage n-1
   Tf* F = fac_global<Tf>(B, s);
   for (int e = tid; e < nv * nv; e += NT) {
     const int i = e / nv, j = e - i * nv;
-    F[e] = (j <= i) ? sPhi[e] : (Tf)0;
+    F[e] = j > i ? (Tf)0 : (i < ne ? sMt[i * ne + j] : sPhi[i * ldP + j]);
   }
   for (int e = tid; e < nk * nk; e += NT) {
     const int i = e / nk, j = e - i * nk;
-    sL[i * nk + j] = (j <= i) ? sPhi[(ne + i) * nv + ne + j] : (Tf)0;
+    sL[i * nk + j] = (j <= i) ? sPhi[(ne + i) * ldP + ne + j] : (Tf)0;
   }
   return ok;
 }
@@ -488,20 +644,14 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     }
     if (n < C.N) {
       // va = L_{n+1}' rb_n
-      for (int k = tid; k < nx1; k += NT) {
-        Tf acc = 0;
-        for (int j = k; j < nx1; ++j) acc += sL[j * nx1 + k] * (Tf)rb[s.eq + j];
-        va[k] = acc;
-      }
+      for (int k = tid; k < nx1; k += NT)
+        va[k] = dot4<Tf>(k, nx1, [&](int j) { return sL[j * nx1 + k] * (Tf)rb[s.eq + j]; });
     }
     __syncthreads();
     if (n < C.N) {
       // vb = L_{n+1} va + p_{n+1}
-      for (int k = tid; k < nx1; k += NT) {
-        Tf acc = pn1[k];
-        for (int j = 0; j <= k; ++j) acc += sL[k * nx1 + j] * va[j];
-        vb[k] = acc;
-      }
+      for (int k = tid; k < nx1; k += NT)
+        vb[k] = pn1[k] + dot4<Tf>(0, k + 1, [&](int j) { return sL[k * nx1 + j] * va[j]; });
     }
     __syncthreads();
     // phi = gt_n + [B A]' vb
@@ -515,7 +665,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
       Tf acc = (Tf)gi;
       if (n < C.N) {
         const double* ba = D + L.BAt + (int64_t)i * L.ldb;
-        for (int k = 0; k < nx1; ++k) acc += (Tf)ba[k] * vb[k];
+        acc += dot4<Tf>(0, nx1, [&](int k) { return (Tf)ba[k] * vb[k]; });
       }
       phi[i] = acc;
     }
@@ -524,16 +674,14 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     __syncthreads();
     // l = X phi_e
     for (int i = tid; i < ne; i += NT) {
-      Tf acc = 0;
-      for (int j = 0; j <= i; ++j) acc += F[i * nv + j] * phi[j];
+      const Tf acc = dot4<Tf>(0, i + 1, [&](int j) { return F[i * nv + j] * phi[j]; });
       ln[i] = acc;
       lp[s.var + i] = (double)acc;
     }
     __syncthreads();
     // p_n = phi_k - L_ke l  -> p_{n+1} of stage n-1; L_n = L_kk -> L_{n+1} of stage n-1
     for (int i = tid; i < nk; i += NT) {
-      Tf acc = phi[ne + i];
-      for (int j = 0; j < ne; ++j) acc -= F[(ne + i) * nv + j] * ln[j];
+      const Tf acc = phi[ne + i] - dot4<Tf>(0, ne, [&](int j) { return F[(ne + i) * nv + j] * ln[j]; });
       pn1[i] = acc;
       lp[s.var + ne + i] = (double)acc;
     }
@@ -554,42 +702,30 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     if (n > 0) {
       // pi_n = L_n (L_n' x_n) + p_n,  L_n = L_kk of this stage
       const double* xn = yn + ne;
-      for (int k = tid; k < nk; k += NT) {
-        Tf acc = 0;
-        for (int j = k; j < nk; ++j) acc += F[(ne + j) * nv + ne + k] * (Tf)xn[j];
-        va[k] = acc;
-      }
+      for (int k = tid; k < nk; k += NT)
+        va[k] = dot4<Tf>(k, nk, [&](int j) { return F[(ne + j) * nv + ne + k] * (Tf)xn[j]; });
       __syncthreads();
       const int eqp = C.st[n - 1].eq;
       for (int k = tid; k < nk; k += NT) {
-        Tf acc = (Tf)lp[s.var + ne + k];
-        for (int j = 0; j <= k; ++j) acc += F[(ne + k) * nv + ne + j] * va[j];
+        const Tf acc = (Tf)lp[s.var + ne + k] + dot4<Tf>(0, k + 1, [&](int j) { return F[(ne + k) * nv + ne + j] * va[j]; });
         dpi[eqp + k] = (double)acc;
       }
       __syncthreads();
     }
     // va = l + L_ke' x_n
-    for (int j = tid; j < ne; j += NT) {
-      Tf acc = (Tf)lp[s.var + j];
-      for (int i = 0; i < nk; ++i) acc += F[(ne + i) * nv + j] * (Tf)yn[ne + i];
-      va[j] = acc;
-    }
+    for (int j = tid; j < ne; j += NT)
+      va[j] = (Tf)lp[s.var + j] + dot4<Tf>(0, nk, [&](int i) { return F[(ne + i) * nv + j] * (Tf)yn[ne + i]; });
     __syncthreads();
     // y_e = -X' va
-    for (int i = tid; i < ne; i += NT) {
-      Tf acc = 0;
-      for (int j = i; j < ne; ++j) acc += F[j * nv + i] * va[j];
-      yn[i] = -(double)acc;
-    }
+    for (int i = tid; i < ne; i += NT)
+      yn[i] = -(double)dot4<Tf>(i, ne, [&](int j) { return F[j * nv + i] * va[j]; });
     __syncthreads();
     if (n < C.N) {
       // x_{n+1} = [B A] y_n + rb_n
       double* x1 = dy + C.st[n + 1].var + C.st[n + 1].nu;
-      for (int k = tid; k < nx1; k += NT) {
-        Tf acc = (Tf)rb[s.eq + k];
-        for (int i = 0; i < nv; ++i) acc += (Tf)D[L.BAt + (int64_t)i * L.ldb + k] * (Tf)yn[i];
-        x1[k] = (double)acc;
-      }
+      for (int k = tid; k < nx1; k += NT)
+        x1[k] = (double)((Tf)rb[s.eq + k] +
+                         dot4<Tf>(0, nv, [&](int i) { return (Tf)D[L.BAt + (int64_t)i * L.ldb + k] * (Tf)yn[i]; }));
     }
     // dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt) on active sides
     for (int c = tid; c < nc; c += NT) {
@@ -848,6 +984,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
   int status = GQ_STATUS_MAX_ITER, it = 0, flags = 0;
   Count cnt;
   bool fp64 = !mixed;
+  int lifted_at = -1;  // iteration whose lambda, t were lifted after a lost FP64 pivot
   double alpha = 1.0;
   Norms r{0, 0, 0, 0};
   const Dir d{B.dy, B.dpi, B.dlam, B.dt};
@@ -887,10 +1024,36 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
     for_sides(C, [&](int i) { B.rm[i] = B.lam[i] * B.t[i]; });
     __syncthreads();
     const double reg = fp64 ? (mixed ? 0.0 : arg.reg_prim) : arg.reg_prim;
-    const bool ok = fp64 ? factor<double>(C, reg) : factor<float>(C, reg);
+    bool ok = fp64 ? factor<double>(C, reg) : factor<float>(C, reg);
     ++cnt.fact;
     cnt.fact64 += fp64;
-    const int okall = (int)block_reduce(ok ? 1.0 : 0.0, red, OpMin());
+    int okall = (int)block_reduce(ok ? 1.0 : 0.0, red, OpMin());
+    if (!okall && fp64 && reg < kRegRetry) {
+      // an FP64 pivot lost positivity in the end game: regularise the primal
+      // block (Sec. 4.2, regularisation) and factor once more
+      ok = factor<double>(C, kRegRetry);
+      ++cnt.fact;
+      ++cnt.fact64;
+      flags |= GQ_FLAG_REGULARIZED;
+      okall = (int)block_reduce(ok ? 1.0 : 0.0, red, OpMin());
+    }
+    if (!okall && fp64 && lifted_at != it) {
+      // still indefinite: complementarity ran far ahead of stationarity and
+      // barrier weights lambda/t near 1/t_min swamp Phi.  Lift lambda and t
+      // of active sides to a floor tied to the stationarity residual (moving
+      // r_d by no more than that floor) and redo this iteration
+      lifted_at = it;
+      const double floor_lt = fmax(kLift, kLiftRel * fmax(r.g, r.b));
+      flags |= GQ_FLAG_REGULARIZED;
+      for_sides(C, [&](int i) {
+        if (B.lam[i] != 0.0) {
+          B.lam[i] = fmax(B.lam[i], floor_lt);
+          B.t[i] = fmax(B.t[i], floor_lt);
+        }
+      });
+      __syncthreads();
+      continue;
+    }
     if (!okall) {
       if (!fp64 && arg.fp64_fallback) {
         fp64 = true;
@@ -996,8 +1159,10 @@ cudaError_t launch_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, c
     if (e != cudaSuccess) return e;
     attr_bytes = smem;
   }
-  int nt = ((sh.nvmax + 31) / 32) * 32;
-  nt = nt < 32 ? 32 : (nt > 256 ? 256 : nt);
+  // 256 threads whatever the stage size: the micro-tiled products and the
+  // trailing Cholesky updates have work for all of them (measured faster
+  // than one thread per stage row on the ragged and large-stage workloads)
+  const int nt = 256;
   DirOut o{};
   if (out) o = *out;
   ipm_kernel<<<count, nt, smem, stream>>>(b, sh, arg, (int)kind, sigma_mu, o, order);

@@ -25,12 +25,16 @@ struct Shape {
   int32_t pad;
 };
 
+// Row stride of the block kernel's Phi and M' tiles: nv rounded up to 4.
+__host__ __device__ inline int block_ld(int nv) { return (nv + 3) & ~3; }
+
 // Elements (doubles) of the block kernel's stage-matrix scratch for a shape:
-// L_{n+1} (nxmax^2), Phi (nvmax^2), M or X (nvmax x max(nxmax, ne_max)).
+// L_{n+1} (nxmax^2), Phi (nvmax x block_ld), M' or X (wide x block_ld with
+// wide = max(nxmax, ne_max)).
 __host__ __device__ inline int64_t block_mat_elems(const Shape& sh) {
   const int wide = sh.nxmax > sh.ne_max ? sh.nxmax : sh.ne_max;
-  return ((int64_t)sh.nxmax * sh.nxmax + (int64_t)sh.nvmax * sh.nvmax + (int64_t)sh.nvmax * (wide > 0 ? wide : 1) +
-          15) & ~int64_t(15);
+  const int64_t ld = block_ld(sh.nvmax);
+  return ((int64_t)sh.nxmax * sh.nxmax + (int64_t)sh.nvmax * ld + ld * (wide > 0 ? wide : 1) + 15) & ~int64_t(15);
 }
 
 // QPs whose stages all have nu + nx <= 32 and nx <= 32 run one per warp.

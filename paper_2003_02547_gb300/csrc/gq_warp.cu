@@ -31,6 +31,9 @@ using namespace dev;
 
 constexpr int LDS = 33;                 // shared-memory row stride
 constexpr double kIrFailRatio = 1e-6;   // mixed path: refinement residual ratio that hands the QP to FP64
+constexpr double kLift = 1e-10;          // smallest floor of lambda, t after a lost FP64 pivot
+constexpr double kLiftRel = 1e-2;        // ... relative to the stationarity residual
+constexpr double kRegRetry = 1e-10;     // primal regularisation of an FP64 refactorisation after a lost pivot
 constexpr double kInexact = 0.1;        // mixed path: direction residual allowed per unit of iterate residual
 
 __device__ __forceinline__ StageData wlay(const StageDesc& s) {
@@ -820,6 +823,7 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
     cnt.solve = stats->n_solve;
     cnt.res = stats->n_res;
   }
+  int lifted_at = -1;  // iteration whose lambda, t were lifted after a lost FP64 pivot
   double alpha = 1.0;
   WNorms r{0, 0, 0, 0};
   const WDir d{B.dy, B.dpi, B.dlam, B.dt};
@@ -856,10 +860,36 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
     for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) B.rm[i] = B.lam[i] * B.t[i];
     set_tinv();
     const double reg = fp64 ? (mixed ? 0.0 : arg.reg_prim) : arg.reg_prim;
-    const bool ok = wfactor<T>(C, reg);
+    bool ok = wfactor<T>(C, reg);
     ++cnt.fact;
     cnt.fact64 += fp64;
-    const bool okall = __all_sync(kFull, ok);
+    bool okall = __all_sync(kFull, ok);
+    if (!okall && fp64 && reg < kRegRetry) {
+      // an FP64 pivot lost positivity in the end game: regularise the primal
+      // block (Sec. 4.2, regularisation) and factor once more
+      ok = wfactor<T>(C, kRegRetry);
+      ++cnt.fact;
+      ++cnt.fact64;
+      flags |= GQ_FLAG_REGULARIZED;
+      okall = __all_sync(kFull, ok);
+    }
+    if (!okall && fp64 && lifted_at != it) {
+      // still indefinite: complementarity ran far ahead of stationarity and
+      // barrier weights lambda/t near 1/t_min swamp Phi.  Lift lambda and t
+      // of active sides to a floor tied to the stationarity residual (moving
+      // r_d by no more than that floor) and redo this iteration
+      lifted_at = it;
+      const double floor_lt = fmax(kLift, kLiftRel * fmax(r.g, r.b));
+      flags |= GQ_FLAG_REGULARIZED;
+      for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) {
+        if (B.lam[i] != 0.0) {
+          B.lam[i] = fmax(B.lam[i], floor_lt);
+          B.t[i] = fmax(B.t[i], floor_lt);
+        }
+      }
+      __syncwarp();
+      continue;
+    }
     if (!okall) {
       if (!fp64 && arg.fp64_fallback) {
         status = kStatusResumeFp64;

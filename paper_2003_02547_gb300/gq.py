@@ -15,6 +15,7 @@ GQ_OK = 0
 GQ_ERR_ARG, GQ_ERR_DIMS, GQ_ERR_SIZE, GQ_ERR_CUDA, GQ_ERR_DATA, GQ_ERR_STATE = -1, -2, -3, -4, -5, -6
 STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_MIN_STEP, STATUS_NAN, STATUS_TIMEOUT = 0, 1, 2, 3, 4
 FLAG_FP64_FALLBACK = 1
+FLAG_REGULARIZED = 2
 MODE_SPEED, MODE_BALANCE = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
