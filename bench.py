@@ -184,7 +184,7 @@ def launches_per_solve(qps, arg) -> int:
 # ----------------------------------------------------------------------------
 # serving: open-loop Poisson arrivals through the continuous-batching server
 # ----------------------------------------------------------------------------
-def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: int = 4, max_batch: int = 512):
+def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: int = 16, max_batch: int = 512):
     """Arrivals drawn like the ragged workload (30 % repeats of an earlier key
     with x0 + N(0, 0.01^2), warm-started from the resident iterate), every
     request packed on the host before its arrival time, submitted at its
@@ -227,6 +227,7 @@ def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: in
         "iters_cold_hist": np.bincount(iters[~warm], minlength=1).tolist(),
         "batches": rep["batches"], "mean_batch": rep["batched_qps"] / max(1, rep["batches"]),
         "max_lanes_busy": rep["max_lanes_busy"], "max_queue": rep["max_queue"],
+        "cold_retries": rep["cold_retries"],
         "budget_gb": budget_gb, "lanes": lanes, "max_batch": max_batch,
         "wall_s": (t_end - t0) * 1e-9,
     }
@@ -446,7 +447,7 @@ def main():
         extras["serving"] = serving_run(a.serving_rate, a.serving_duration)
         # the same request mix below the ragged batch capacity: latency
         # without a standing queue
-        light = 0.7 * extras["ragged_4096_mixed"]["value"]
+        light = 0.5 * extras["ragged_4096_mixed"]["value"]
         extras["serving_below_capacity"] = serving_run(light, max(1.0, 600.0 / light))
 
     if rank == 0:

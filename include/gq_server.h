@@ -26,6 +26,10 @@
  * one place this library allocates host memory; it never allocates device
  * memory.
  *
+ * Warm starts.  A warm-started request that does not converge is solved once
+ * more from a cold start (its resident iterate is dropped; latency counts
+ * both attempts); gq_ticket_info.warm_used then reads 0.
+ *
  * Ordering.  Requests with the same non-zero key are solved in submission
  * order, one at a time: a request whose key is still being solved waits in
  * the queue (other requests pass it), so a warm start always reads the
@@ -91,6 +95,7 @@ typedef struct gq_server_report {
     int64_t deferrals;                 /* requests passed over while their key was busy  */
     int64_t max_lanes_busy;
     int64_t max_queue;
+    int64_t cold_retries;              /* warm starts that did not converge, re-solved cold */
 } gq_server_report;
 
 /* Default configuration: 4 lanes, max_batch 256, max_wait_us 0, device 0,

@@ -39,7 +39,7 @@
 static_assert(sizeof(gq_server_cfg) == 16 + 8 + sizeof(gq_ipm_arg), "gq_server_cfg layout");
 static_assert(sizeof(gq_request) == 64, "gq_request layout");
 static_assert(sizeof(gq_ticket_info) == 32 + sizeof(gq_stats), "gq_ticket_info layout");
-static_assert(sizeof(gq_server_report) == 14 * 8, "gq_server_report layout");
+static_assert(sizeof(gq_server_report) == 15 * 8, "gq_server_report layout");
 
 namespace {
 
@@ -69,6 +69,7 @@ struct Req {
   gq_request r;
   int64_t ticket;
   int64_t t_arr;
+  int32_t attempt;  // 1 after a warm start that did not converge was re-queued cold
 };
 
 struct Ticket {
@@ -303,14 +304,44 @@ void retire(gq_server* s, Lane& L) {
   }
   L.pinned_ids.clear();
   const int64_t t_done = std::max(t_done_base, now_ns());
+  // a warm start that did not converge is solved once more from a cold start
+  // (its resident iterate is dropped); it keeps its arrival time
+  std::vector<Req> retry;
+  if (L.launch_code == GQ_OK) {
+    for (size_t j = 0; j < L.reqs.size(); ++j) {
+      const gq_stats* st = reinterpret_cast<const gq_stats*>(sol + b->L.stats) + j;
+      if (L.warm_used[j] && st->status != GQ_STATUS_CONVERGED && L.reqs[j].attempt == 0) {
+        Req r = L.reqs[j];
+        r.attempt = 1;
+        r.r.warm = 0;
+        retry.push_back(r);
+        auto it = s->where.find(r.r.key);
+        if (it != s->where.end()) {
+          Entry* e = entry_by_id(s, it->second);
+          if (e && e->live) {
+            e->live = false;
+            s->rep.cache_entries--;
+          }
+          s->where.erase(it);
+        }
+      }
+    }
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
+    size_t k = 0;
     for (size_t j = 0; j < L.reqs.size(); ++j) {
+      if (L.reqs[j].r.key) s->busy_keys.erase(L.reqs[j].r.key);
+      if (k < retry.size() && retry[k].ticket == L.reqs[j].ticket) {
+        ++k;
+        continue;
+      }
       const gq_stats* st =
           L.launch_code == GQ_OK ? reinterpret_cast<const gq_stats*>(sol + b->L.stats) + j : nullptr;
       complete_ticket(s, L.reqs[j], L.launch_code, st, L.warm_used[j], (int)L.reqs.size(), L.t_admit, t_done);
-      if (L.reqs[j].r.key) s->busy_keys.erase(L.reqs[j].r.key);
     }
+    for (size_t j = retry.size(); j-- > 0;) s->pending.push_front(retry[j]);
+    s->rep.cold_retries += (int64_t)retry.size();
   }
   s->cv_done.notify_all();
   L.reqs.clear();
@@ -668,6 +699,7 @@ int gq_server_submit(gq_server* s, const gq_request* req, int64_t* ticket) {
   Req r;
   r.r = *req;
   r.t_arr = req->t_arrival_ns > 0 ? req->t_arrival_ns : now_ns();
+  r.attempt = 0;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->broken || s->stop) return set_error(GQ_ERR_STATE, "server stopped");

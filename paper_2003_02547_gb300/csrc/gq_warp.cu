@@ -247,6 +247,59 @@ __device__ WNorms wresiduals(WCtx& C) {
 }
 
 // ---------------------------------------------------------------------------
+// Warp-level tensor-core products for the FP32 factor: mma.sync m16n8k8 with
+// TF32 operands and FP32 accumulation, each FP32 operand split into a TF32
+// high part and a TF32 remainder ("3xTF32": hi*hi + hi*lo + lo*hi), which
+// keeps the products at FP32 accuracy.  A stage product is at most 32 x 32
+// with k <= 32 here, a handful of 16 x 8 tiles per warp; the CTA-wide tcgen05
+// path needs M >= 64 tiles from shared-memory descriptors and does not fit a
+// warp that owns one QP.
+// Fragment layout (PTX ISA, mma.m16n8k8, .tf32): with g = lane / 4 and
+// q = lane % 4, A holds (g, q), (g + 8, q), (g, q + 4), (g + 8, q + 4); B holds
+// (k = q, n = g), (k = q + 4, n = g); C holds (g, 2q), (g, 2q + 1), (g + 8, 2q),
+// (g + 8, 2q + 1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_hi(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+struct Tf32Pair {
+  uint32_t hi, lo;
+};
+
+__device__ __forceinline__ Tf32Pair tf32_split(float x) {
+  Tf32Pair p;
+  p.hi = tf32_hi(x);
+  p.lo = tf32_hi(x - __uint_as_float(p.hi));
+  return p;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// c += A(16 x 8 tile) * B(8 x 8 tile) in 3xTF32; fa(r, k) and fb(k, n) give
+// the tile elements (zero outside the matrices)
+template <class FA, class FB>
+__device__ __forceinline__ void mma3_tile(float (&c)[4], int lane, FA fa, FB fb) {
+  const int g = lane >> 2, q = lane & 3;
+  const Tf32Pair a0 = tf32_split(fa(g, q)), a1 = tf32_split(fa(g + 8, q));
+  const Tf32Pair a2 = tf32_split(fa(g, q + 4)), a3 = tf32_split(fa(g + 8, q + 4));
+  const Tf32Pair b0 = tf32_split(fb(q, g)), b1 = tf32_split(fb(q + 4, g));
+  const uint32_t ahi[4] = {a0.hi, a1.hi, a2.hi, a3.hi}, alo[4] = {a0.lo, a1.lo, a2.lo, a3.lo};
+  const uint32_t bhi[2] = {b0.hi, b1.hi}, blo[2] = {b0.lo, b1.lo};
+  mma_tf32(c, alo, bhi);
+  mma_tf32(c, ahi, blo);
+  mma_tf32(c, ahi, bhi);
+}
+
+// ---------------------------------------------------------------------------
 // a3: square-root Riccati factorisation of one stage, lane i <-> row i.
 // Compact loops over shared-memory matrices (odd stride, conflict-free): the
 // code stays small enough for the instruction cache, which a fully unrolled
@@ -274,8 +327,41 @@ __device__ __forceinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double
     if (D[L.hi + c] != INFINITY) w += B.lam[s.side + nc + c] * B.tinv[s.side + nc + c];
     sw[c] = (T)w;
   }
+  constexpr bool kMma = sizeof(T) == 4;
   // M row i: M[i][j] = sum_{k >= j} [B A]'[i][k] L_{n+1}[k][j]
-  if (n < C.N && act) {
+  if constexpr (kMma) {
+    if (n < C.N) {
+    // tensor-core tiles: rows of [B A]' by columns of L_{n+1} (lower
+    // triangular, so k-steps left of the diagonal block are skipped)
+    const float* ba = reinterpret_cast<const float*>(D) + L.BAt;
+    const float* lf = reinterpret_cast<const float*>(sL);
+    const int ldb = L.ldb;
+    const int g = lane >> 2, q = lane & 3;
+    for (int mt = 0; mt * 16 < nv; ++mt) {
+      for (int nt = 0; nt * 8 < nx1; ++nt) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int kt = nt; kt * 8 < nx1; ++kt) {
+          mma3_tile(
+              c, lane,
+              [&](int r, int k) {
+                const int ii = mt * 16 + r, kk = kt * 8 + k;
+                return (ii < nv && kk < nx1) ? ba[ii * ldb + kk] : 0.f;
+              },
+              [&](int k, int j) {
+                const int kk = kt * 8 + k, jj = nt * 8 + j;
+                return (kk < nx1 && jj < nx1) ? lf[kk * LDS + jj] : 0.f;
+              });
+        }
+        float* mf = reinterpret_cast<float*>(sM);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int ii = mt * 16 + g + (e >> 1) * 8, jj = nt * 8 + 2 * q + (e & 1);
+          if (ii < nv && jj < nx1) mf[ii * LDS + jj] = c[e];
+        }
+      }
+    }
+    }
+  } else if (n < C.N && act) {
     const T* ba = D + L.BAt + (int64_t)i * L.ldb;
     for (int j = 0; j < nx1; ++j) {
       T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
@@ -292,7 +378,60 @@ __device__ __forceinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double
   }
   __syncwarp();
   // Phi row i (lower part): RSQ + M M' + [D C]' diag(w_g) [D C] + diagonal terms
-  if (act) {
+  if constexpr (kMma) {
+    // tensor-core tiles of the lower triangle: M M' over k < nx1, then the
+    // general rows' [D C]' W [D C] over k < ng
+    const float* mf = reinterpret_cast<const float*>(sM);
+    const float* dcf = reinterpret_cast<const float*>(D) + L.DC;
+    const float* rsf = reinterpret_cast<const float*>(D) + L.RSQ;
+    const float* swf = reinterpret_cast<const float*>(sw);
+    float* pf = reinterpret_cast<float*>(sP);
+    const int ldr = L.ldr, ng = s.ng;
+    const bool prod = n < C.N;
+    const int g = lane >> 2, q = lane & 3;
+    for (int mt = 0; mt * 16 < nv; ++mt) {
+      for (int nt = 0; nt * 8 < nv && nt * 8 <= mt * 16 + 15; ++nt) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+        if (prod) {
+          for (int kt = 0; kt * 8 < nx1; ++kt) {
+            mma3_tile(
+                c, lane,
+                [&](int r, int k) {
+                  const int ii = mt * 16 + r, kk = kt * 8 + k;
+                  return (ii < nv && kk < nx1) ? mf[ii * LDS + kk] : 0.f;
+                },
+                [&](int k, int j) {
+                  const int kk = kt * 8 + k, jj = nt * 8 + j;
+                  return (kk < nx1 && jj < nv) ? mf[jj * LDS + kk] : 0.f;
+                });
+          }
+        }
+        for (int kt = 0; kt * 8 < ng; ++kt) {
+          mma3_tile(
+              c, lane,
+              [&](int r, int k) {
+                const int ii = mt * 16 + r, kk = kt * 8 + k;
+                return (ii < nv && kk < ng) ? dcf[kk * nv + ii] * swf[nb + kk] : 0.f;
+              },
+              [&](int k, int j) {
+                const int kk = kt * 8 + k, jj = nt * 8 + j;
+                return (kk < ng && jj < nv) ? dcf[kk * nv + jj] : 0.f;
+              });
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int ii = mt * 16 + g + (e >> 1) * 8, jj = nt * 8 + 2 * q + (e & 1);
+          if (ii < nv && jj <= ii) pf[ii * LDS + jj] = rsf[ii * ldr + jj] + c[e];
+        }
+      }
+    }
+    __syncwarp();
+    if (act) {
+      T dadd = (T)reg;
+      if (nb > 0 && bmap[i] >= 0) dadd += sw[bmap[i]];
+      sP[i * LDS + i] += dadd;
+    }
+  } else if (act) {
     const T* rs = D + L.RSQ + (int64_t)i * L.ldr;
     const T* mi = sM + i * LDS;
     const bool prod = n < C.N;

@@ -69,7 +69,7 @@ class TicketInfo(ctypes.Structure):
 class ServerReport(ctypes.Structure):
     _fields_ = [(n, c_int64) for n in ("submitted", "completed", "rejected", "failed", "batches", "batched_qps",
                                        "warm_hits", "warm_misses", "cache_entries", "cache_evictions",
-                                       "cache_skips", "deferrals", "max_lanes_busy", "max_queue")]
+                                       "cache_skips", "deferrals", "max_lanes_busy", "max_queue", "cold_retries")]
 
 
 # name -> (restype, argtypes); the same names and order as include/gq.h and

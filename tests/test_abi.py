@@ -52,7 +52,7 @@ def test_struct_sizes_match_header(gqmod):
     assert ctypes.sizeof(gqmod.ServerCfg) == 4 * 4 + 8 + ctypes.sizeof(gqmod.IpmArg)
     assert ctypes.sizeof(gqmod.Request) == 8 + 4 + 4 + 8 + 8 + 4 * 8
     assert ctypes.sizeof(gqmod.TicketInfo) == 4 * 4 + 2 * 8 + 64
-    assert ctypes.sizeof(gqmod.ServerReport) == 14 * 8
+    assert ctypes.sizeof(gqmod.ServerReport) == 15 * 8
 
 
 def test_arg_defaults(gqmod):

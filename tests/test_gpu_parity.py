@@ -319,3 +319,7 @@ def test_mass_spring_full_batch(env, precision):
     sample = set(range(0, 1024, 97)) | {1023}
     refs = [oracle_pair(q) if i in sample else None for i, q in enumerate(qps)]
     _check_converged(b, qps, refs)
+    if precision == 1:
+        # the FP32 factors plus refinement suffice on this workload: a QP
+        # handed to FP64 would mean inaccurate FP32 factors
+        assert not np.any(b.all_stats()["flags"] & 1)
