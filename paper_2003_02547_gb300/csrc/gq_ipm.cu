@@ -166,6 +166,55 @@ __device__ double fixed_sum(const Ctx& C, int count, F f) {
   return r;
 }
 
+// Sum of f(k) for k in [k0, k1) in four interleaved partial sums (a fixed
+// order that depends on k0, k1 only): short dependent FMA chains.
+template <typename Tf, class F>
+__device__ __forceinline__ Tf dot4(int k0, int k1, F f) {
+  Tf a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  int k = k0;
+  for (; k + 3 < k1; k += 4) {
+    a0 += f(k);
+    a1 += f(k + 1);
+    a2 += f(k + 2);
+    a3 += f(k + 3);
+  }
+  for (; k < k1; ++k) a0 += f(k);
+  return (a0 + a1) + (a2 + a3);
+}
+
+// Row-parallel dot products: for every row r < nrows, out(r, sum of term(r, k)
+// over k in [lo(r), hi(r))).  Each row gets tpr consecutive lanes (8, 4, 2 or 1
+// so that all rows fit the block at once when they can); lane `sub` of a
+// group sums k = lo + sub, lo + sub + tpr, ... in four interleaved partial
+// sums, and the group combines by a butterfly.  The order depends on the
+// row's range and tpr only (tpr on nrows and blockDim), and every warp runs
+// the same number of rounds, so all shuffles are warp-uniform.
+template <typename V, class Lo, class Hi, class Term, class Out>
+__device__ __forceinline__ void rows_dot(int nrows, Lo lo, Hi hi, Term term, Out out) {
+  const int NT = blockDim.x, tid = threadIdx.x;
+  const int tpr = nrows * 8 <= NT ? 8 : (nrows * 4 <= NT ? 4 : (nrows * 2 <= NT ? 2 : 1));
+  const int groups = NT / tpr, sub = tid & (tpr - 1);
+  const int rounds = (nrows + groups - 1) / groups;
+  for (int m = 0; m < rounds; ++m) {
+    const int r = m * groups + tid / tpr;
+    V a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    if (r < nrows) {
+      const int k1 = hi(r), st = 4 * tpr;
+      int k = lo(r) + sub;
+      for (; k + 3 * tpr < k1; k += st) {
+        a0 += term(r, k);
+        a1 += term(r, k + tpr);
+        a2 += term(r, k + 2 * tpr);
+        a3 += term(r, k + 3 * tpr);
+      }
+      for (; k < k1; k += tpr) a0 += term(r, k);
+    }
+    V acc = (a0 + a1) + (a2 + a3);
+    for (int o = 1; o < tpr; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (r < nrows && sub == 0) out(r, acc);
+  }
+}
+
 __device__ __forceinline__ StageData lay(const StageDesc& s) {
   return stage_data_layout(s.nx, s.nu, s.nx1, s.nbu + s.nbx, s.ng);
 }
@@ -264,52 +313,38 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
   const double* yn = y + s.var;
   const double* lm = lam + s.side;
   const int32_t* bmap = box_idx(D, L) + nb;
-  for (int i = tid; i < nv; i += NT) {
-    // four partial sums per dot product: FP64 FMA latency dominates a
-    // single dependent chain
-    const double* row = D + L.RSQ + (int64_t)i * L.ldr;
-    double a[4] = {0.0, 0.0, 0.0, 0.0};
-    int j = 0;
-    for (; j + 3 < nv; j += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = fma(row[j + u], yn[j + u], a[u]);
-    }
-    for (; j < nv; ++j) a[0] = fma(row[j], yn[j], a[0]);
-    if (n < C.N) {
-      const double* ba = D + L.BAt + (int64_t)i * L.ldb;
-      const double* pn1 = pi + s.eq;
-      int k = 0;
-      for (; k + 3 < nx1; k += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = fma(ba[k + u], pn1[k + u], a[u]);
-      }
-      for (; k < nx1; ++k) a[0] = fma(ba[k], pn1[k], a[0]);
-    }
-    double acc = (lin ? add_g[s.var + i] : D[L.rq + i]) + ((a[0] + a[1]) + (a[2] + a[3]));
-    if (n > 0 && i >= s.nu) acc -= pi[C.st[n - 1].eq + (i - s.nu)];
-    for (int g = 0; g < s.ng; ++g) acc = fma(-D[L.DC + (int64_t)g * nv + i], lm[nb + g] - lm[nc + nb + g], acc);
-    if (nb > 0) {
-      const int c = bmap[i];
-      if (c >= 0) acc -= lm[c] - lm[nc + c];
-    }
-    og[s.var + i] = acc;
-    mx.g = max_nan(mx.g, fabs(acc));
+  // r_g rows: [RSQ row | [B A]' row] . [y_n | pi_{n+1}], then the rest
+  {
+    const double* pn1 = pi + s.eq;
+    const int kend = n < C.N ? nv + nx1 : nv;
+    rows_dot<double>(
+        nv, [&](int) { return 0; }, [&](int) { return kend; },
+        [&](int i, int k) {
+          return k < nv ? D[L.RSQ + (int64_t)i * L.ldr + k] * yn[k] : D[L.BAt + (int64_t)i * L.ldb + (k - nv)] * pn1[k - nv];
+        },
+        [&](int i, double v) {
+          double acc = (lin ? add_g[s.var + i] : D[L.rq + i]) + v;
+          if (n > 0 && i >= s.nu) acc -= pi[C.st[n - 1].eq + (i - s.nu)];
+          for (int g = 0; g < s.ng; ++g)
+            acc = fma(-D[L.DC + (int64_t)g * nv + i], lm[nb + g] - lm[nc + nb + g], acc);
+          if (nb > 0) {
+            const int c = bmap[i];
+            if (c >= 0) acc -= lm[c] - lm[nc + c];
+          }
+          og[s.var + i] = acc;
+          mx.g = max_nan(mx.g, fabs(acc));
+        });
   }
   if (n < C.N) {
     const double* yn1 = y + C.st[n + 1].var + C.st[n + 1].nu;
-    for (int k = tid; k < nx1; k += NT) {
-      double a[4] = {0.0, 0.0, 0.0, 0.0};
-      int i = 0;
-      for (; i + 3 < nv; i += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = fma(D[L.BAt + (int64_t)(i + u) * L.ldb + k], yn[i + u], a[u]);
-      }
-      for (; i < nv; ++i) a[0] = fma(D[L.BAt + (int64_t)i * L.ldb + k], yn[i], a[0]);
-      double acc = (lin ? add_b[s.eq + k] : D[L.b + k]) + ((a[0] + a[1]) + (a[2] + a[3]));
-      acc -= yn1[k];
-      ob[s.eq + k] = acc;
-      mx.b = max_nan(mx.b, fabs(acc));
-    }
+    rows_dot<double>(
+        nx1, [&](int) { return 0; }, [&](int) { return nv; },
+        [&](int k, int i) { return D[L.BAt + (int64_t)i * L.ldb + k] * yn[i]; },
+        [&](int k, double v) {
+          const double acc = (lin ? add_b[s.eq + k] : D[L.b + k]) + v - yn1[k];
+          ob[s.eq + k] = acc;
+          mx.b = max_nan(mx.b, fabs(acc));
+        });
   }
   if (rd != nullptr) {
     for (int c = tid; c < nc; c += NT) {
@@ -358,22 +393,6 @@ __device__ Norms residuals(Ctx& C) {
 // blockDim.
 constexpr int kT = 4;
 constexpr int kPanel = 8;
-
-// Sum of f(k) for k in [k0, k1) in four interleaved partial sums (a fixed
-// order that depends on k0, k1 only): short dependent FMA chains.
-template <typename Tf, class F>
-__device__ __forceinline__ Tf dot4(int k0, int k1, F f) {
-  Tf a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-  int k = k0;
-  for (; k + 3 < k1; k += 4) {
-    a0 += f(k);
-    a1 += f(k + 1);
-    a2 += f(k + 2);
-    a3 += f(k + 3);
-  }
-  for (; k < k1; ++k) a0 += f(k);
-  return (a0 + a1) + (a2 + a3);
-}
 
 // lower-triangle tile index -> (I, J), J <= I
 __device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
@@ -644,47 +663,54 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     }
     if (n < C.N) {
       // va = L_{n+1}' rb_n
-      for (int k = tid; k < nx1; k += NT)
-        va[k] = dot4<Tf>(k, nx1, [&](int j) { return sL[j * nx1 + k] * (Tf)rb[s.eq + j]; });
+      rows_dot<Tf>(
+          nx1, [&](int k) { return k; }, [&](int) { return nx1; },
+          [&](int k, int j) { return sL[j * nx1 + k] * (Tf)rb[s.eq + j]; }, [&](int k, Tf v) { va[k] = v; });
     }
     __syncthreads();
     if (n < C.N) {
       // vb = L_{n+1} va + p_{n+1}
-      for (int k = tid; k < nx1; k += NT)
-        vb[k] = pn1[k] + dot4<Tf>(0, k + 1, [&](int j) { return sL[k * nx1 + j] * va[j]; });
+      rows_dot<Tf>(
+          nx1, [&](int) { return 0; }, [&](int k) { return k + 1; },
+          [&](int k, int j) { return sL[k * nx1 + j] * va[j]; }, [&](int k, Tf v) { vb[k] = pn1[k] + v; });
     }
     __syncthreads();
     // phi = gt_n + [B A]' vb
-    for (int i = tid; i < nv; i += NT) {
-      double gi = g[s.var + i];
-      if (rd != nullptr) {
-        for (int gg = 0; gg < s.ng; ++gg) gi = fma(-D[L.DC + (int64_t)gg * nv + i], vs[nb + gg], gi);
-        if (nb > 0 && bmap[i] >= 0) gi -= vs[bmap[i]];
-      }
-      scale = max_nan(scale, fabs(gi));
-      Tf acc = (Tf)gi;
-      if (n < C.N) {
-        const double* ba = D + L.BAt + (int64_t)i * L.ldb;
-        acc += dot4<Tf>(0, nx1, [&](int k) { return (Tf)ba[k] * vb[k]; });
-      }
-      phi[i] = acc;
+    {
+      const int kend = n < C.N ? nx1 : 0;
+      rows_dot<Tf>(
+          nv, [&](int) { return 0; }, [&](int) { return kend; },
+          [&](int i, int k) { return (Tf)D[L.BAt + (int64_t)i * L.ldb + k] * vb[k]; },
+          [&](int i, Tf v) {
+            double gi = g[s.var + i];
+            if (rd != nullptr) {
+              for (int gg = 0; gg < s.ng; ++gg) gi = fma(-D[L.DC + (int64_t)gg * nv + i], vs[nb + gg], gi);
+              if (nb > 0 && bmap[i] >= 0) gi -= vs[bmap[i]];
+            }
+            scale = max_nan(scale, fabs(gi));
+            phi[i] = (Tf)gi + v;
+          });
     }
     if (n < C.N)
       for (int k = tid; k < nx1; k += NT) scale = max_nan(scale, fabs(rb[s.eq + k]));
     __syncthreads();
     // l = X phi_e
-    for (int i = tid; i < ne; i += NT) {
-      const Tf acc = dot4<Tf>(0, i + 1, [&](int j) { return F[i * nv + j] * phi[j]; });
-      ln[i] = acc;
-      lp[s.var + i] = (double)acc;
-    }
+    rows_dot<Tf>(
+        ne, [&](int) { return 0; }, [&](int i) { return i + 1; }, [&](int i, int j) { return F[i * nv + j] * phi[j]; },
+        [&](int i, Tf v) {
+          ln[i] = v;
+          lp[s.var + i] = (double)v;
+        });
     __syncthreads();
     // p_n = phi_k - L_ke l  -> p_{n+1} of stage n-1; L_n = L_kk -> L_{n+1} of stage n-1
-    for (int i = tid; i < nk; i += NT) {
-      const Tf acc = phi[ne + i] - dot4<Tf>(0, ne, [&](int j) { return F[(ne + i) * nv + j] * ln[j]; });
-      pn1[i] = acc;
-      lp[s.var + ne + i] = (double)acc;
-    }
+    rows_dot<Tf>(
+        nk, [&](int) { return 0; }, [&](int) { return ne; },
+        [&](int i, int j) { return F[(ne + i) * nv + j] * ln[j]; },
+        [&](int i, Tf v) {
+          const Tf acc = phi[ne + i] - v;
+          pn1[i] = acc;
+          lp[s.var + ne + i] = (double)acc;
+        });
     for (int e = tid; e < nk * nk; e += NT) {
       const int i = e / nk, j = e - i * nk;
       sL[i * nk + j] = F[(ne + i) * nv + ne + j];
@@ -702,30 +728,35 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     if (n > 0) {
       // pi_n = L_n (L_n' x_n) + p_n,  L_n = L_kk of this stage
       const double* xn = yn + ne;
-      for (int k = tid; k < nk; k += NT)
-        va[k] = dot4<Tf>(k, nk, [&](int j) { return F[(ne + j) * nv + ne + k] * (Tf)xn[j]; });
+      rows_dot<Tf>(
+          nk, [&](int k) { return k; }, [&](int) { return nk; },
+          [&](int k, int j) { return F[(ne + j) * nv + ne + k] * (Tf)xn[j]; }, [&](int k, Tf v) { va[k] = v; });
       __syncthreads();
       const int eqp = C.st[n - 1].eq;
-      for (int k = tid; k < nk; k += NT) {
-        const Tf acc = (Tf)lp[s.var + ne + k] + dot4<Tf>(0, k + 1, [&](int j) { return F[(ne + k) * nv + ne + j] * va[j]; });
-        dpi[eqp + k] = (double)acc;
-      }
+      rows_dot<Tf>(
+          nk, [&](int) { return 0; }, [&](int k) { return k + 1; },
+          [&](int k, int j) { return F[(ne + k) * nv + ne + j] * va[j]; },
+          [&](int k, Tf v) { dpi[eqp + k] = (double)((Tf)lp[s.var + ne + k] + v); });
       __syncthreads();
     }
     // va = l + L_ke' x_n
-    for (int j = tid; j < ne; j += NT)
-      va[j] = (Tf)lp[s.var + j] + dot4<Tf>(0, nk, [&](int i) { return F[(ne + i) * nv + j] * (Tf)yn[ne + i]; });
+    rows_dot<Tf>(
+        ne, [&](int) { return 0; }, [&](int) { return nk; },
+        [&](int j, int i) { return F[(ne + i) * nv + j] * (Tf)yn[ne + i]; },
+        [&](int j, Tf v) { va[j] = (Tf)lp[s.var + j] + v; });
     __syncthreads();
     // y_e = -X' va
-    for (int i = tid; i < ne; i += NT)
-      yn[i] = -(double)dot4<Tf>(i, ne, [&](int j) { return F[j * nv + i] * va[j]; });
+    rows_dot<Tf>(
+        ne, [&](int i) { return i; }, [&](int) { return ne; }, [&](int i, int j) { return F[j * nv + i] * va[j]; },
+        [&](int i, Tf v) { yn[i] = -(double)v; });
     __syncthreads();
     if (n < C.N) {
       // x_{n+1} = [B A] y_n + rb_n
       double* x1 = dy + C.st[n + 1].var + C.st[n + 1].nu;
-      for (int k = tid; k < nx1; k += NT)
-        x1[k] = (double)((Tf)rb[s.eq + k] +
-                         dot4<Tf>(0, nv, [&](int i) { return (Tf)D[L.BAt + (int64_t)i * L.ldb + k] * (Tf)yn[i]; }));
+      rows_dot<Tf>(
+          nx1, [&](int) { return 0; }, [&](int) { return nv; },
+          [&](int k, int i) { return (Tf)D[L.BAt + (int64_t)i * L.ldb + k] * (Tf)yn[i]; },
+          [&](int k, Tf v) { x1[k] = (double)((Tf)rb[s.eq + k] + v); });
     }
     // dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt) on active sides
     for (int c = tid; c < nc; c += NT) {
