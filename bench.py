@@ -268,7 +268,7 @@ def batch_run(qps, dev, precision: int, reps: int = 2):
 # profiles/).  It is reported only while the kernel sources hash to the
 # value recorded with the capture; after any change it reads null.
 TRAFFIC_CAPTURE = {"sha256": "e3c43664bc036e12ba8a910141bb735656679a23368202b5f80d9b34669dc300", "bytes": 6028772000}
-KERNEL_SOURCES = ["gq_warp.cu", "gq_device.h", "gq_internal.h", "gq_launch.h"]
+KERNEL_SOURCES = ["gq_warp.cu", "gq_device.h", "gq_internal.h", "gq_launch.h", "gq_mma.h"]
 
 
 def kernel_sources_sha256() -> str:

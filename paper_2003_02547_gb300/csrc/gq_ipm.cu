@@ -41,6 +41,7 @@
 #include "gq_device.h"
 #include "gq_internal.h"
 #include "gq_launch.h"
+#include "gq_mma.h"
 
 namespace gq {
 
@@ -59,6 +60,7 @@ __host__ __device__ SmemPlan smem_plan(const Batch& b, const Shape& sh) {
   p.chunk = take((size_t)((sh.nside_max + 31) / 32 + 1) * sizeof(double), 16);
   p.vec = take((size_t)8 * p.vmax * sizeof(double), 16);
   p.mat = sh.mat_global ? 0 : take((size_t)block_mat_elems(sh) * sizeof(double), 16);
+  p.panel = take((size_t)(sh.nvmax > 0 ? sh.nvmax : 1) * kBlockPanel * sizeof(double), 16);
   p.stages = take((size_t)sh.nst_max * sizeof(StageDesc), 16);
   // ring: two buffers of (data block + FP64-sized factor block)
   p.ring_fac = (size_t)((sh.data_max * 8 + 127) / 128 * 128);
@@ -132,6 +134,7 @@ struct Ctx {
   double* chunk;  // per-32-side partial sums for fixed_sum
   double* vbuf;   // vector scratch (8 * vmax doubles)
   int vmax;
+  void* panel;  // shared-memory copy of one Cholesky column panel (nv x kBlockPanel, Tf)
   void* mat;  // matrix scratch (Tf): L_{n+1}, Phi, M
   int nvmax, nxmax;
   Ring ring;
@@ -392,7 +395,7 @@ __device__ Norms residuals(Ctx& C) {
 // output's sum runs in a fixed order, so the result does not depend on
 // blockDim.
 constexpr int kT = 4;
-constexpr int kPanel = 8;
+constexpr int kPanel = kBlockPanel;
 
 // lower-triangle tile index -> (I, J), J <= I
 __device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
@@ -427,127 +430,238 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
     if (D[L.hi + c] != INFINITY) w += lm[nc + c] / tt[nc + c];
     sw[c] = (Tf)w;
   }
-  const int nI = (nv + kT - 1) / kT;
-  // M' = ([B A]' L_{n+1})': Mt[j][i] = sum_{k >= j} BAt[i][k] L[k][j]
-  if (n < C.N) {
-    const int nJ = (nx1 + kT - 1) / kT;
-    for (int t = tid; t < nI * nJ; t += NT) {
-      const int I = t / nJ, J = t - I * nJ;
-      Tf acc[kT][kT] = {};
-      const double* ba[kT];
-#pragma unroll
-      for (int r = 0; r < kT; ++r) ba[r] = D + L.BAt + (int64_t)min(I * kT + r, nv - 1) * L.ldb;
-      for (int k = J * kT; k < nx1; ++k) {
-        Tf a[kT], bb[kT];
-#pragma unroll
-        for (int r = 0; r < kT; ++r) a[r] = (Tf)ba[r][k];
-#pragma unroll
-        for (int c = 0; c < kT; ++c) bb[c] = J * kT + c < nx1 ? sL[k * nx1 + J * kT + c] : (Tf)0;
-#pragma unroll
-        for (int r = 0; r < kT; ++r)
-#pragma unroll
-          for (int c = 0; c < kT; ++c) acc[r][c] += a[r] * bb[c];
-      }
-#pragma unroll
-      for (int c = 0; c < kT; ++c) {
-        const int j = J * kT + c;
-        if (j < nx1) {
-#pragma unroll
-          for (int r = 0; r < kT; ++r)
-            if (I * kT + r < nv) sMt[j * ldP + I * kT + r] = acc[r][c];
-        }
-      }
-    }
-  }
-  __syncthreads();
-  // Phi = RSQ + reg I + W_box + [D C]' diag(w_g) [D C] + M M'   (lower tiles)
-  for (int t = tid; t < nI * (nI + 1) / 2; t += NT) {
-    int I, J;
-    tri_tile(t, I, J);
-    Tf acc[kT][kT];
-#pragma unroll
-    for (int r = 0; r < kT; ++r) {
-      const int i = min(I * kT + r, nv - 1);
-#pragma unroll
-      for (int c = 0; c < kT; ++c) {
-        const int j = min(J * kT + c, nv - 1);
-        const int hi = i > j ? i : j, lo = i > j ? j : i;
-        acc[r][c] = (Tf)D[L.RSQ + (int64_t)hi * L.ldr + lo];
-      }
-    }
-    for (int g = 0; g < s.ng; ++g) {
-      const double* row = D + L.DC + (int64_t)g * nv;
-      const Tf wg = sw[nb + g];
-      Tf a[kT], bb[kT];
-#pragma unroll
-      for (int r = 0; r < kT; ++r) a[r] = (Tf)row[min(I * kT + r, nv - 1)] * wg;
-#pragma unroll
-      for (int c = 0; c < kT; ++c) bb[c] = (Tf)row[min(J * kT + c, nv - 1)];
-#pragma unroll
-      for (int r = 0; r < kT; ++r)
-#pragma unroll
-        for (int c = 0; c < kT; ++c) acc[r][c] += a[r] * bb[c];
-    }
+  if constexpr (sizeof(Tf) == 4) {
+    // FP32 factor: both products on the tensor cores (3xTF32 mma.sync), each
+    // warp owning 16-row strips of 4 n-tiles (16 x 32 outputs)
+    const int lane = tid & 31, w = tid >> 5, NW = NT >> 5;
+    const int g = lane >> 2, q = lane & 3;
+    const int nMT = (nv + 15) / 16;
     if (n < C.N) {
-      for (int k = 0; k < nx1; ++k) {
-        const Tf* mk = sMt + k * ldP;
-        Tf a[kT], bb[kT];
+      // M = [B A]' L_{n+1} (L lower: k-steps left of an n-tile are zero), stored as M'
+      const int nNT = (nx1 + 7) / 8, nNG = (nNT + 3) / 4;
+      for (int u = w; u < nMT * nNG; u += NW) {
+        const int mt = u / nNG, nt0 = (u - mt * nNG) * 4;
+        float c[4][4] = {};
+        for (int kt = nt0; kt * 8 < nx1; ++kt) {
+          auto fa = [&](int r, int k) {
+            const int ii = mt * 16 + r, kk = kt * 8 + k;
+            return (ii < nv && kk < nx1) ? (float)D[L.BAt + (int64_t)ii * L.ldb + kk] : 0.f;
+          };
+          const Tf32Pair a0 = tf32_split(fa(g, q)), a1 = tf32_split(fa(g + 8, q));
+          const Tf32Pair a2 = tf32_split(fa(g, q + 4)), a3 = tf32_split(fa(g + 8, q + 4));
+          const uint32_t ahi[4] = {a0.hi, a1.hi, a2.hi, a3.hi}, alo[4] = {a0.lo, a1.lo, a2.lo, a3.lo};
 #pragma unroll
-        for (int r = 0; r < kT; ++r) a[r] = mk[min(I * kT + r, nv - 1)];
+          for (int jn = 0; jn < 4; ++jn) {
+            const int nt = nt0 + jn;
+            if (nt >= nNT || kt < nt) continue;
+            auto fb = [&](int k, int j) {
+              const int kk = kt * 8 + k, jj = nt * 8 + j;
+              return (kk < nx1 && jj < nx1) ? (float)sL[kk * nx1 + jj] : 0.f;
+            };
+            const Tf32Pair b0 = tf32_split(fb(q, g)), b1 = tf32_split(fb(q + 4, g));
+            const uint32_t bhi[2] = {b0.hi, b1.hi}, blo[2] = {b0.lo, b1.lo};
+            mma_tf32(c[jn], alo, bhi);
+            mma_tf32(c[jn], ahi, blo);
+            mma_tf32(c[jn], ahi, bhi);
+          }
+        }
 #pragma unroll
-        for (int c = 0; c < kT; ++c) bb[c] = mk[min(J * kT + c, nv - 1)];
+        for (int jn = 0; jn < 4; ++jn)
 #pragma unroll
-        for (int r = 0; r < kT; ++r)
-#pragma unroll
-          for (int c = 0; c < kT; ++c) acc[r][c] += a[r] * bb[c];
+          for (int e = 0; e < 4; ++e) {
+            const int ii = mt * 16 + g + (e >> 1) * 8, jj = (nt0 + jn) * 8 + 2 * q + (e & 1);
+            if (ii < nv && jj < nx1) sMt[jj * ldP + ii] = (Tf)c[jn][e];
+          }
       }
     }
+    __syncthreads();
+    // Phi = RSQ + M M' + [D C]' W [D C] + diagonal terms, lower strips
+    {
+      const int nNT = (nv + 7) / 8, nNG = (nNT + 3) / 4;
+      const int kend = n < C.N ? nx1 : 0;
+      for (int u = w; u < nMT * nNG; u += NW) {
+        const int mt = u / nNG, nt0 = (u - mt * nNG) * 4;
+        if (nt0 * 8 > mt * 16 + 15) continue;  // strip above the diagonal
+        float c[4][4] = {};
+        for (int kt = 0; kt * 8 < kend + s.ng; ++kt) {
+          // k < kend: columns of M (rows of M'); then the general rows
+          auto val = [&](int i, int k) -> float {
+            if (i >= nv) return 0.f;
+            if (k < kend) return (float)sMt[k * ldP + i];
+            const int gg = k - kend;
+            return gg < s.ng ? (float)D[L.DC + (int64_t)gg * nv + i] : 0.f;
+          };
+          auto fa = [&](int r, int k) {
+            const int kk = kt * 8 + k, gg = kk - kend;
+            const float v = val(mt * 16 + r, kk);
+            return (kk >= kend && gg < s.ng) ? v * (float)sw[nb + gg] : v;
+          };
+          const Tf32Pair a0 = tf32_split(fa(g, q)), a1 = tf32_split(fa(g + 8, q));
+          const Tf32Pair a2 = tf32_split(fa(g, q + 4)), a3 = tf32_split(fa(g + 8, q + 4));
+          const uint32_t ahi[4] = {a0.hi, a1.hi, a2.hi, a3.hi}, alo[4] = {a0.lo, a1.lo, a2.lo, a3.lo};
 #pragma unroll
-    for (int r = 0; r < kT; ++r) {
-      const int i = I * kT + r;
-#pragma unroll
-      for (int c = 0; c < kT; ++c) {
-        const int j = J * kT + c;
-        if (i < nv && j <= i) {
-          Tf v = acc[r][c];
-          if (i == j) {
-            v += (Tf)reg;
-            if (nb > 0 && bmap[i] >= 0) v += sw[bmap[i]];
+          for (int jn = 0; jn < 4; ++jn) {
+            const int nt = nt0 + jn;
+            if (nt >= nNT || nt * 8 > mt * 16 + 15) continue;
+            const Tf32Pair b0 = tf32_split(val(nt * 8 + g, kt * 8 + q)), b1 = tf32_split(val(nt * 8 + g, kt * 8 + q + 4));
+            const uint32_t bhi[2] = {b0.hi, b1.hi}, blo[2] = {b0.lo, b1.lo};
+            mma_tf32(c[jn], alo, bhi);
+            mma_tf32(c[jn], ahi, blo);
+            mma_tf32(c[jn], ahi, bhi);
           }
-          sPhi[i * ldP + j] = v;
+        }
+#pragma unroll
+        for (int jn = 0; jn < 4; ++jn)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int ii = mt * 16 + g + (e >> 1) * 8, jj = (nt0 + jn) * 8 + 2 * q + (e & 1);
+            if (ii < nv && jj <= ii) {
+              Tf v = (Tf)D[L.RSQ + (int64_t)ii * L.ldr + jj] + (Tf)c[jn][e];
+              if (ii == jj) {
+                v += (Tf)reg;
+                if (nb > 0 && bmap[ii] >= 0) v += sw[bmap[ii]];
+              }
+              sPhi[ii * ldP + jj] = v;
+            }
+          }
+      }
+    }
+    __syncthreads();
+  } else {
+  const int nI = (nv + kT - 1) / kT;
+    // M' = ([B A]' L_{n+1})': Mt[j][i] = sum_{k >= j} BAt[i][k] L[k][j]
+    if (n < C.N) {
+      const int nJ = (nx1 + kT - 1) / kT;
+      for (int t = tid; t < nI * nJ; t += NT) {
+        const int I = t / nJ, J = t - I * nJ;
+        Tf acc[kT][kT] = {};
+        const double* ba[kT];
+  #pragma unroll
+        for (int r = 0; r < kT; ++r) ba[r] = D + L.BAt + (int64_t)min(I * kT + r, nv - 1) * L.ldb;
+        for (int k = J * kT; k < nx1; ++k) {
+          Tf a[kT], bb[kT];
+  #pragma unroll
+          for (int r = 0; r < kT; ++r) a[r] = (Tf)ba[r][k];
+  #pragma unroll
+          for (int c = 0; c < kT; ++c) bb[c] = J * kT + c < nx1 ? sL[k * nx1 + J * kT + c] : (Tf)0;
+  #pragma unroll
+          for (int r = 0; r < kT; ++r)
+  #pragma unroll
+            for (int c = 0; c < kT; ++c) acc[r][c] += a[r] * bb[c];
+        }
+  #pragma unroll
+        for (int c = 0; c < kT; ++c) {
+          const int j = J * kT + c;
+          if (j < nx1) {
+  #pragma unroll
+            for (int r = 0; r < kT; ++r)
+              if (I * kT + r < nv) sMt[j * ldP + I * kT + r] = acc[r][c];
+          }
         }
       }
     }
+    __syncthreads();
+    // Phi = RSQ + reg I + W_box + [D C]' diag(w_g) [D C] + M M'   (lower tiles)
+    for (int t = tid; t < nI * (nI + 1) / 2; t += NT) {
+      int I, J;
+      tri_tile(t, I, J);
+      Tf acc[kT][kT];
+  #pragma unroll
+      for (int r = 0; r < kT; ++r) {
+        const int i = min(I * kT + r, nv - 1);
+  #pragma unroll
+        for (int c = 0; c < kT; ++c) {
+          const int j = min(J * kT + c, nv - 1);
+          const int hi = i > j ? i : j, lo = i > j ? j : i;
+          acc[r][c] = (Tf)D[L.RSQ + (int64_t)hi * L.ldr + lo];
+        }
+      }
+      for (int g = 0; g < s.ng; ++g) {
+        const double* row = D + L.DC + (int64_t)g * nv;
+        const Tf wg = sw[nb + g];
+        Tf a[kT], bb[kT];
+  #pragma unroll
+        for (int r = 0; r < kT; ++r) a[r] = (Tf)row[min(I * kT + r, nv - 1)] * wg;
+  #pragma unroll
+        for (int c = 0; c < kT; ++c) bb[c] = (Tf)row[min(J * kT + c, nv - 1)];
+  #pragma unroll
+        for (int r = 0; r < kT; ++r)
+  #pragma unroll
+          for (int c = 0; c < kT; ++c) acc[r][c] += a[r] * bb[c];
+      }
+      if (n < C.N) {
+        for (int k = 0; k < nx1; ++k) {
+          const Tf* mk = sMt + k * ldP;
+          Tf a[kT], bb[kT];
+  #pragma unroll
+          for (int r = 0; r < kT; ++r) a[r] = mk[min(I * kT + r, nv - 1)];
+  #pragma unroll
+          for (int c = 0; c < kT; ++c) bb[c] = mk[min(J * kT + c, nv - 1)];
+  #pragma unroll
+          for (int r = 0; r < kT; ++r)
+  #pragma unroll
+            for (int c = 0; c < kT; ++c) acc[r][c] += a[r] * bb[c];
+        }
+      }
+  #pragma unroll
+      for (int r = 0; r < kT; ++r) {
+        const int i = I * kT + r;
+  #pragma unroll
+        for (int c = 0; c < kT; ++c) {
+          const int j = J * kT + c;
+          if (i < nv && j <= i) {
+            Tf v = acc[r][c];
+            if (i == j) {
+              v += (Tf)reg;
+              if (nb > 0 && bmap[i] >= 0) v += sw[bmap[i]];
+            }
+            sPhi[i * ldP + j] = v;
+          }
+        }
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  // blocked right-looking Cholesky: one warp factors each kPanel-wide column
-  // panel, then all threads apply its rank-kPanel update to the trailing
-  // lower triangle
+  // blocked right-looking Cholesky: each kPanel-wide column panel is copied
+  // to shared memory, factored there by one warp, written back, and its
+  // rank-kPanel update is applied to the trailing lower triangle by all
+  // threads in kT x kT tiles read from the shared copy
   const int lane = tid & 31;
+  Tf* sPan = static_cast<Tf*>(C.panel);  // rows p0..nv-1 of the panel, ld kPanel
   for (int p0 = 0; p0 < nv; p0 += kPanel) {
-    const int pw = min(kPanel, nv - p0);
+    const int pw = min(kPanel, nv - p0), pr = nv - p0;
+    for (int e = tid; e < pr * kPanel; e += NT) {
+      const int r = e / kPanel, c = e - r * kPanel;
+      sPan[e] = c < pw ? sPhi[(p0 + r) * ldP + p0 + c] : (Tf)0;
+    }
+    __syncthreads();
     if (tid < 32) {
       for (int c = 0; c < pw; ++c) {
-        const int col = p0 + c;
-        Tf d = sPhi[col * ldP + col];
+        Tf d = sPan[c * kPanel + c];
         if (!(d > (Tf)0)) {
           ok = false;
           d = (Tf)1;
         }
         const Tf lcc = sqrt(d);
         const Tf inv = (Tf)1 / lcc;
-        for (int r = col + 1 + lane; r < nv; r += 32) sPhi[r * ldP + col] *= inv;
+        for (int r = c + 1 + lane; r < pr; r += 32) sPan[r * kPanel + c] *= inv;
         __syncwarp();
-        if (lane == 0) sPhi[col * ldP + col] = lcc;
-        for (int r = col + 1 + lane; r < nv; r += 32) {
-          const Tf lr = sPhi[r * ldP + col];
-          const int cend = min(p0 + pw - 1, r);
-          for (int c2 = col + 1; c2 <= cend; ++c2) sPhi[r * ldP + c2] -= lr * sPhi[c2 * ldP + col];
+        if (lane == 0) sPan[c * kPanel + c] = lcc;
+        for (int r = c + 1 + lane; r < pr; r += 32) {
+          const Tf lr = sPan[r * kPanel + c];
+          const int cend = min(pw - 1, r);
+          for (int c2 = c + 1; c2 <= cend; ++c2) sPan[r * kPanel + c2] -= lr * sPan[c2 * kPanel + c];
         }
         __syncwarp();
       }
     }
     __syncthreads();
+    // write the factored panel back (lower part) ...
+    for (int e = tid; e < pr * pw; e += NT) {
+      const int r = e / pw, c = e - r * pw;
+      if (c <= r) sPhi[(p0 + r) * ldP + p0 + c] = sPan[r * kPanel + c];
+    }
+    // ... and apply its update to the trailing lower triangle
     const int q0 = p0 + pw, m = nv - q0;
     if (m > 0) {
       const int nQ = (m + kT - 1) / kT;
@@ -559,10 +673,11 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
         const Tf* rj[kT];
 #pragma unroll
         for (int r = 0; r < kT; ++r) {
-          ri[r] = sPhi + min(q0 + I * kT + r, nv - 1) * ldP + p0;
-          rj[r] = sPhi + min(q0 + J * kT + r, nv - 1) * ldP + p0;
+          ri[r] = sPan + (min(q0 + I * kT + r, nv - 1) - p0) * kPanel;
+          rj[r] = sPan + (min(q0 + J * kT + r, nv - 1) - p0) * kPanel;
         }
-        for (int c = 0; c < pw; ++c) {
+#pragma unroll
+        for (int c = 0; c < kPanel; ++c) {
           Tf a[kT], bb[kT];
 #pragma unroll
           for (int r = 0; r < kT; ++r) {
@@ -584,8 +699,8 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
           }
         }
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
   ok = __syncthreads_and(ok) != 0;
   // X = L_ee^{-1} (lower), column j by thread j, into the M' buffer (ld ne)
@@ -909,6 +1024,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
                         : static_cast<void*>(smem + P.mat);
   C.nvmax = sh.nvmax;
   C.nxmax = sh.nxmax;
+  C.panel = smem + P.panel;
   C.ring.buf[0] = smem + P.ring0;
   C.ring.buf[1] = smem + P.ring1;
   C.ring.bar = bars;

@@ -25,6 +25,9 @@ struct Shape {
   int32_t pad;
 };
 
+// Column width of the block kernel's Cholesky panels.
+constexpr int kBlockPanel = 8;
+
 // Row stride of the block kernel's Phi and M' tiles: nv rounded up to 4.
 __host__ __device__ inline int block_ld(int nv) { return (nv + 3) & ~3; }
 
@@ -52,7 +55,7 @@ constexpr size_t kMaxSmem = 227 * 1024;
 
 // Dynamic shared-memory plan of the IPM kernel (byte offsets).
 struct SmemPlan {
-  size_t bars, red, chunk, vec, mat, stages, ring0, ring1, ring_fac, bytes;
+  size_t bars, red, chunk, vec, mat, panel, stages, ring0, ring1, ring_fac, bytes;
   int vmax;
   bool staged;  // stage blocks go through the bulk-copy ring
 };
