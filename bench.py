@@ -184,7 +184,7 @@ def launches_per_solve(qps, arg) -> int:
 # ----------------------------------------------------------------------------
 # serving: open-loop Poisson arrivals through the continuous-batching server
 # ----------------------------------------------------------------------------
-def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: int = 16, max_batch: int = 512):
+def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: int = 4, max_batch: int = 512):
     """Arrivals drawn like the ragged workload (30 % repeats of an earlier key
     with x0 + N(0, 0.01^2), warm-started from the resident iterate), every
     request packed on the host before its arrival time, submitted at its
@@ -267,7 +267,7 @@ def batch_run(qps, dev, precision: int, reps: int = 2):
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; summary in
 # profiles/).  It is reported only while the kernel sources hash to the
 # value recorded with the capture; after any change it reads null.
-TRAFFIC_CAPTURE = {"sha256": "e3c43664bc036e12ba8a910141bb735656679a23368202b5f80d9b34669dc300", "bytes": 6028772000}
+TRAFFIC_CAPTURE = {"sha256": "9cafd5d003241bd61089ad37c1137bea0a29a00352db829cea3a3ca974e8ae50", "bytes": 6033957000}
 KERNEL_SOURCES = ["gq_warp.cu", "gq_device.h", "gq_internal.h", "gq_launch.h", "gq_mma.h"]
 
 

@@ -1298,13 +1298,12 @@ cudaError_t launch_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, c
   if (count <= 0) return cudaSuccess;
   const size_t smem = ipm_smem_bytes(b, sh);
   if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
-  // opt in to the dynamic shared memory this launch needs (per process; the
-  // attribute only ever grows)
-  static size_t attr_bytes = 48 * 1024;
-  if (smem > attr_bytes) {
+  // opt in to the dynamic shared memory this launch needs (set on the current
+  // device at every launch above the default: no cache shared between host
+  // threads or devices)
+  if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(ipm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_bytes = smem;
   }
   // 256 threads whatever the stage size: the micro-tiled products and the
   // trailing Cholesky updates have work for all of them (measured faster

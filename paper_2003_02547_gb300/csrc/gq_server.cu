@@ -125,6 +125,9 @@ struct gq_server {
   gq_server_report rep;
 
   // worker-private
+  struct {
+    int64_t warm_hits = 0, warm_misses = 0, cache_entries = 0, cache_evictions = 0, cache_skips = 0;
+  } wc;  // cache counters, copied into rep under mu by the worker
   std::deque<Entry> ring;
   int64_t ring_next_id = 0;
   int64_t head = 0;
@@ -154,8 +157,8 @@ bool evict_front(gq_server* s) {
   if (e.live) {
     auto it = s->where.find(e.key);
     if (it != s->where.end() && it->second == e.id) s->where.erase(it);
-    s->rep.cache_evictions++;
-    s->rep.cache_entries--;
+    s->wc.cache_evictions++;
+    s->wc.cache_entries--;
   }
   s->ring.pop_front();
   return true;
@@ -191,7 +194,7 @@ int64_t cache_alloc(gq_server* s, int64_t len, uint64_t key, int64_t nvt, int64_
   e.live = true;
   s->ring.push_back(e);
   s->head = start + len;
-  s->rep.cache_entries++;
+  s->wc.cache_entries++;
   return e.id;
 }
 
@@ -320,7 +323,7 @@ void retire(gq_server* s, Lane& L) {
           Entry* e = entry_by_id(s, it->second);
           if (e && e->live) {
             e->live = false;
-            s->rep.cache_entries--;
+            s->wc.cache_entries--;
           }
           s->where.erase(it);
         }
@@ -476,16 +479,16 @@ int launch_lane(gq_server* s, Lane& L, std::vector<Req>& reqs) {
           ops[ngather++] = CopyOp{e->off + q.nvt + q.neqt + q.nsidet, ot + q.side0, q.nsidet};
           e->pins++;
           L.pinned_ids.push_back(e->id);
-          s->rep.warm_hits++;
+          s->wc.warm_hits++;
         } else {
-          s->rep.warm_misses++;
+          s->wc.warm_misses++;
         }
       }
       if (e && e->live) {
         // superseded by this request's solution
         e->live = false;
         s->where.erase(r.key);
-        s->rep.cache_entries--;
+        s->wc.cache_entries--;
       }
       const int64_t len = q.nvt + q.neqt + 2 * (int64_t)q.nsidet;
       const int64_t id = cache_alloc(s, len, r.key, q.nvt, q.neqt, q.nsidet);
@@ -499,10 +502,10 @@ int launch_lane(gq_server* s, Lane& L, std::vector<Req>& reqs) {
         scatter.push_back(CopyOp{olam + q.side0, ne->off + q.nvt + q.neqt, q.nsidet});
         scatter.push_back(CopyOp{ot + q.side0, ne->off + q.nvt + q.neqt + q.nsidet, q.nsidet});
       } else {
-        s->rep.cache_skips++;
+        s->wc.cache_skips++;
       }
     } else if (r.warm) {
-      s->rep.warm_misses++;
+      s->wc.warm_misses++;
     }
     hq[j].warm = level + 1;  // explicit per-QP level (cold = 0)
     b->qp[j].warm = level + 1;
@@ -574,6 +577,11 @@ void worker_main(gq_server* s) {
       broken = s->broken;
       if (broken) fail_all_pending(s, GQ_ERR_CUDA);
       if (busy > s->rep.max_lanes_busy) s->rep.max_lanes_busy = busy;
+      s->rep.warm_hits = s->wc.warm_hits;
+      s->rep.warm_misses = s->wc.warm_misses;
+      s->rep.cache_entries = s->wc.cache_entries;
+      s->rep.cache_evictions = s->wc.cache_evictions;
+      s->rep.cache_skips = s->wc.cache_skips;
     }
     if (!broken) {
       for (Lane& L : s->lanes) {
