@@ -56,6 +56,10 @@ typedef struct gq_server_cfg {
                              warm-start iterates (0: no warm starts)                    */
     gq_ipm_arg arg;       /* solver arguments of every micro-batch (warm_start is set
                              per request)                                                */
+    double class_ratio;   /* size classes: a micro-batch takes only requests whose
+                             factorisation cost estimate lies in the same power of
+                             class_ratio as the oldest eligible request's, so small
+                             QPs do not wait for the largest (<= 1: no classes)      */
 } gq_server_cfg;
 
 typedef struct gq_request {
@@ -99,7 +103,7 @@ typedef struct gq_server_report {
 } gq_server_report;
 
 /* Default configuration: 4 lanes, max_batch 256, max_wait_us 0, device 0,
- * cache_bytes 0, arg = gq_ipm_arg_default(SPEED, MIXED). */
+ * cache_bytes 0, arg = gq_ipm_arg_default(SPEED, MIXED), class_ratio 4. */
 GQ_API int gq_server_cfg_default(gq_server_cfg* cfg);
 
 /* Creates the server and starts its worker thread.  dev_arena (256-byte

@@ -20,6 +20,7 @@
 #include <time.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -36,7 +37,7 @@
 #include "../../include/gq_server.h"
 #include "gq_batch.h"
 
-static_assert(sizeof(gq_server_cfg) == 16 + 8 + sizeof(gq_ipm_arg), "gq_server_cfg layout");
+static_assert(sizeof(gq_server_cfg) == 16 + 8 + sizeof(gq_ipm_arg) + 8, "gq_server_cfg layout");
 static_assert(sizeof(gq_request) == 64, "gq_request layout");
 static_assert(sizeof(gq_ticket_info) == 32 + sizeof(gq_stats), "gq_ticket_info layout");
 static_assert(sizeof(gq_server_report) == 15 * 8, "gq_server_report layout");
@@ -70,6 +71,7 @@ struct Req {
   int64_t ticket;
   int64_t t_arr;
   int32_t attempt;  // 1 after a warm start that did not converge was re-queued cold
+  int32_t cls;      // size class (power of class_ratio of the cost estimate)
 };
 
 struct Ticket {
@@ -363,10 +365,19 @@ bool take(gq_server* s, std::vector<Req>* out, bool force) {
   if (s->pending.empty()) return false;
   std::unordered_set<uint64_t> chosen;
   std::vector<std::list<Req>::iterator> its;
+  bool have_cls = false;
+  int cls = 0;
   for (auto it = s->pending.begin(); it != s->pending.end() && (int)its.size() < s->cfg.max_batch; ++it) {
     const uint64_t k = it->r.key;
     if (k && (s->busy_keys.count(k) || chosen.count(k))) {
       s->rep.deferrals++;
+      continue;
+    }
+    // the oldest eligible request sets the micro-batch's size class
+    if (!have_cls) {
+      have_cls = true;
+      cls = it->cls;
+    } else if (it->cls != cls) {
       continue;
     }
     if (k) chosen.insert(k);
@@ -640,6 +651,7 @@ int gq_server_cfg_default(gq_server_cfg* cfg) {
   cfg->max_wait_us = 0;
   cfg->device = 0;
   cfg->cache_bytes = 0;
+  cfg->class_ratio = 4.0;
   return gq_ipm_arg_default(&cfg->arg, GQ_MODE_SPEED, GQ_PREC_MIXED);
 }
 
@@ -708,6 +720,11 @@ int gq_server_submit(gq_server* s, const gq_request* req, int64_t* ticket) {
   r.r = *req;
   r.t_arr = req->t_arrival_ns > 0 ? req->t_arrival_ns : now_ns();
   r.attempt = 0;
+  r.cls = 0;
+  if (s->cfg.class_ratio > 1.0) {
+    const double c = src->qp[req->src_qp].cost;
+    r.cls = (int32_t)std::floor(std::log(c > 1.0 ? c : 1.0) / std::log(s->cfg.class_ratio));
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->broken || s->stop) return set_error(GQ_ERR_STATE, "server stopped");

@@ -51,7 +51,8 @@ class Sizes(ctypes.Structure):
 
 class ServerCfg(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_wait_us", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("cache_bytes", c_size_t), ("arg", IpmArg)]
+                ("device", ctypes.c_int32), ("cache_bytes", c_size_t), ("arg", IpmArg),
+                ("class_ratio", c_double)]
 
 
 class Request(ctypes.Structure):

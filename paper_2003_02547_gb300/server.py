@@ -19,7 +19,7 @@ from . import gq
 class Server:
     def __init__(self, budget_bytes: int, lanes: int = 4, max_batch: int = 256, max_wait_us: int = 0,
                  cache_bytes: Optional[int] = None, pinned_bytes: Optional[int] = None,
-                 arg: Optional[gq.IpmArg] = None, device: int = 0):
+                 arg: Optional[gq.IpmArg] = None, device: int = 0, class_ratio: Optional[float] = None):
         import torch
         self.lib = gq.load()
         cfg = gq.ServerCfg()
@@ -33,6 +33,8 @@ class Server:
         cfg.cache_bytes = int(cache_bytes)
         if arg is not None:
             cfg.arg = arg
+        if class_ratio is not None:
+            cfg.class_ratio = float(class_ratio)
         self.cfg = cfg
         if pinned_bytes is None:
             # inputs + solutions of one lane are a small part of its device share

@@ -49,7 +49,7 @@ def test_binding_names_match_header(gqmod):
 def test_struct_sizes_match_header(gqmod):
     assert ctypes.sizeof(gqmod.IpmArg) == 8 * 4 + 12 * 8 + 8
     assert ctypes.sizeof(gqmod.Stats) == 64
-    assert ctypes.sizeof(gqmod.ServerCfg) == 4 * 4 + 8 + ctypes.sizeof(gqmod.IpmArg)
+    assert ctypes.sizeof(gqmod.ServerCfg) == 4 * 4 + 8 + ctypes.sizeof(gqmod.IpmArg) + 8
     assert ctypes.sizeof(gqmod.Request) == 8 + 4 + 4 + 8 + 8 + 4 * 8
     assert ctypes.sizeof(gqmod.TicketInfo) == 4 * 4 + 2 * 8 + 64
     assert ctypes.sizeof(gqmod.ServerReport) == 15 * 8
@@ -186,6 +186,7 @@ def test_server_create_validates_before_any_cuda_call(gqmod):
     cfg = gqmod.ServerCfg()
     assert lib.gq_server_cfg_default(ctypes.byref(cfg)) == 0
     assert cfg.lanes == 4 and cfg.max_batch == 256 and cfg.arg.precision == gqmod.PREC_MIXED
+    assert cfg.class_ratio == 4.0
     out = ctypes.c_void_p()
     buf = np.zeros(1 << 16, dtype=np.uint8)
     base = buf.ctypes.data + ((-buf.ctypes.data) % 256)

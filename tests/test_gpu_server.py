@@ -177,3 +177,26 @@ def test_lanes_overlap_and_keys_stay_ordered(env):
         # visible on the host
         assert arrivals[24 + i] + second.wait_ns >= arrivals[i] + first.latency_ns
         assert second.stats.iters <= first.stats.iters
+
+
+@pytest.mark.parametrize("class_ratio", [4.0, 1.0])
+def test_size_classes_group_micro_batches(env, class_ratio):
+    """With size classes a micro-batch takes only requests of the oldest
+    eligible request's cost class, so small QPs never share a batch (and its
+    completion time) with large ones; class_ratio <= 1 turns this off."""
+    gq, server, QpBatch, torch = env
+    small = [W.small_random_qp(i) for i in range(6)]
+    big = [W.large_stage_qp(i, N=4) for i in range(3)]
+    qps = [q for pair in zip(small, big + [None] * 3) for q in pair if q is not None]
+    src = QpBatch(qps, device=None)
+    is_big = [any(q is b for b in big) for q in qps]
+    with server.Server(1 << 30, lanes=1, max_batch=1000, max_wait_us=200000, class_ratio=class_ratio) as srv:
+        tickets = [srv.submit(src, i) for i in range(len(qps))]
+        srv.drain(120.0)
+        infos = [srv.result(t)[0] for t in tickets]
+    assert all(inf.code == 0 and inf.stats.status == gq.STATUS_CONVERGED for inf in infos)
+    sizes = [inf.batch_size for inf in infos]
+    if class_ratio > 1.0:
+        assert all(sz == (3 if b else 6) for sz, b in zip(sizes, is_big)), sizes
+    else:
+        assert all(sz == 9 for sz in sizes), sizes
