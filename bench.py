@@ -233,6 +233,34 @@ def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: in
     }
 
 
+def single_qp_latency(dev, precision: int, solves: int = 10000):
+    """The single small QP (N=10, nx=4, nu=2) solved alone, back to back,
+    one solve call at a time with its launches included: per-solve latency
+    percentiles from CUDA events around each call."""
+    import numpy as np
+    import torch
+    from paper_2003_02547_gb300 import gq, workloads as W
+    from paper_2003_02547_gb300.batch import QpBatch
+    b = QpBatch([W.small_random_qp(0)], device=dev)
+    arg = gq.default_arg(gq.MODE_SPEED, precision)
+    b.upload()
+    for _ in range(20):
+        b.solve(arg)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(solves)]
+    for e0, e1 in evs:
+        e0.record()
+        b.solve(arg)
+        e1.record()
+    torch.cuda.synchronize()
+    ms = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
+    b.download()
+    torch.cuda.synchronize()
+    st = b.all_stats()
+    return {"solves": solves, "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "solves_per_s": float(1e3 / ms.mean()), "iters": int(st["iters"][0]), "converged": int(st["status"][0] == 0)}
+
+
 def batch_run(qps, dev, precision: int, reps: int = 2):
     """Device-timed solves of one batch in one call (inputs resident)."""
     import numpy as np
@@ -459,6 +487,8 @@ def main():
     extras = {}
     if rank == 0 and world == 1 and not a.no_extras:
         del singles
+        extras["single_small_qp_mixed"] = single_qp_latency(dev, gq.PREC_MIXED)
+        extras["single_small_qp_fp64"] = single_qp_latency(dev, gq.PREC_FP64)
         ragged = W.ragged_batch(4096)
         extras["ragged_4096_mixed"] = batch_run(ragged, dev, gq.PREC_MIXED)
         extras["ragged_4096_fp64"] = batch_run(ragged, dev, gq.PREC_FP64)

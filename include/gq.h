@@ -198,6 +198,20 @@ GQ_API int gq_set_general(gq_batch* b, int qp, int n, const double* C, int ldc, 
 GQ_API int gq_set_guess(gq_batch* b, int qp, const double* y, const double* pi,
                  const double* lam, const double* t);
 
+/* Initial state by elimination (Sec. 2.2 allows stage-wise sizes, so x_0 can
+ * be removed: nx_0 = 0).  Stage 0 of QP `qp` must have nx_0 = 0; given the
+ * measured state x0 (nx0 entries) and the stage-0 data that multiply it --
+ * A0 (nx_1 x nx0, column-major, lda), S0 (nu_0 x nx0, lds), C0 (ng_0 x nx0,
+ * ldc) -- and the unfolded b0, r0, lg0, ug0, this writes
+ *   b_0 = b0 + A0 x0,  r_0 = r0 + S0 x0,  lg_0 = lg0 - C0 x0,  ug_0 = ug0 - C0 x0
+ * into the host staging (an infinite bound stays infinite).  Idempotent:
+ * call it again with a new x0 for the next MPC solve (then gq_upload).
+ * The other stage-0 data (B_0, R_0, boxes on u_0, D_0) come from the usual
+ * setters.  Errors: GQ_ERR_DIMS (nx_0 != 0), GQ_ERR_ARG, GQ_ERR_DATA. */
+GQ_API int gq_set_initial_state(gq_batch* b, int qp, const double* x0, int nx0, const double* A0, int lda,
+                                const double* b0, const double* S0, int lds, const double* r0, const double* C0,
+                                int ldc, const double* lg0, const double* ug0);
+
 /* Copies all stage data of QP src_qp of batch `src` into QP dst_qp of batch
  * `dst` (host staging buffers; identical stage sizes required, else
  * GQ_ERR_DIMS).  Lets a server pack each request once and assemble
@@ -256,6 +270,10 @@ GQ_API int gq_get_stage_sol(const gq_batch* b, int qp, int n, double* u, double*
 GQ_API int gq_get_stats(const gq_batch* b, int qp, gq_stats* out);
 /* Offsets (in doubles) of QP qp's vectors inside the sol buffer:
  * off[0] y, off[1] pi, off[2] lam, off[3] t, and their lengths off[4..7]. */
+/* Status (GQ_STATUS_*) and, if iters is non-NULL, iteration count of every
+ * QP, from the host "sol" buffer after gq_download (arrays of nqp entries). */
+GQ_API int gq_get_statuses(const gq_batch* b, int32_t* status, int32_t* iters);
+
 GQ_API int gq_get_sol_offsets(const gq_batch* b, int qp, int64_t off[8]);
 
 /* Per-thread description of the last error, never NULL. */

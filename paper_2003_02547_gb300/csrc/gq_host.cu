@@ -567,6 +567,48 @@ int gq_set_general(gq_batch* b, int qp, int n, const double* C, int ldc, const d
   return GQ_OK;
 }
 
+int gq_set_initial_state(gq_batch* b, int qp, const double* x0, int nx0, const double* A0, int lda,
+                         const double* b0, const double* S0, int lds, const double* r0, const double* C0, int ldc,
+                         const double* lg0, const double* ug0) {
+  StageDesc* s;
+  int rc = stage_of(b, qp, 0, &s);
+  if (rc) return rc;
+  if (s->nx != 0) return fail(GQ_ERR_DIMS, "stage 0 of QP %d keeps x_0 (nx_0 = %d): nothing to eliminate", qp, s->nx);
+  if (b->qp[qp].N == 0) return fail(GQ_ERR_DIMS, "QP %d has no dynamics to fold x0 into", qp);
+  const int nu = s->nu, nx1 = s->nx1, ng = s->ng, nb = s->nbu + s->nbx;
+  if (nx0 < 0 || (nx0 > 0 && (x0 == nullptr || A0 == nullptr || (nu && S0 == nullptr) || (ng && C0 == nullptr))))
+    return fail(GQ_ERR_ARG, "x0 and its stage-0 matrices must be non-NULL");
+  if (b0 == nullptr || (nu && r0 == nullptr) || (ng && (lg0 == nullptr || ug0 == nullptr)))
+    return fail(GQ_ERR_ARG, "b0, r0, lg0, ug0 must be non-NULL");
+  if (nx0 > 0 && (lda < nx1 || (nu && lds < nu) || (ng && ldc < ng)))
+    return fail(GQ_ERR_ARG, "leading dimension too small");
+  const StageData lay = stage_data_layout(0, nu, nx1, nb, ng);
+  double* D = host_data(b) + s->data;
+  // b_0 + A_0 x0, r_0 + S_0 x0, and the general bounds minus C_0 x0
+  for (int k = 0; k < nx1; ++k) {
+    double v = b0[k];
+    for (int j = 0; j < nx0; ++j) v += A0[k + (int64_t)j * lda] * x0[j];
+    D[lay.b + k] = v;
+  }
+  for (int i = 0; i < nu; ++i) {
+    double v = r0[i];
+    for (int j = 0; j < nx0; ++j) v += S0[i + (int64_t)j * lds] * x0[j];
+    D[lay.rq + i] = v;
+  }
+  for (int g = 0; g < ng; ++g) {
+    double cx = 0.0;
+    for (int j = 0; j < nx0; ++j) cx += C0[g + (int64_t)j * ldc] * x0[j];
+    const double lo = lg0[g] - cx, hi = ug0[g] - cx;  // an infinite bound stays infinite (masked)
+    if (std::isnan(lo) || std::isnan(hi) || lo > hi || lo == INFINITY || hi == -INFINITY)
+      return fail(GQ_ERR_DATA, "general bound %d invalid after folding x0 (lo=%g hi=%g)", g, lo, hi);
+    D[lay.lo + nb + g] = lo;
+    D[lay.hi + nb + g] = hi;
+  }
+  if (!finite_all(D + lay.b, nx1) || !finite_all(D + lay.rq, nu))
+    return fail(GQ_ERR_DATA, "non-finite data after folding x0");
+  return GQ_OK;
+}
+
 int gq_set_guess(gq_batch* b, int qp, const double* y, const double* pi, const double* lam,
                  const double* t) {
   int rc = check_batch(b);
@@ -751,6 +793,19 @@ int gq_get_stats(const gq_batch* b, int qp, gq_stats* out) {
   if (b->host_sol == nullptr) return fail(GQ_ERR_STATE, "host_sol not attached");
   const char* h = static_cast<const char*>(b->host_sol);
   std::memcpy(out, h + b->L.stats + (int64_t)qp * sizeof(gq_stats), sizeof(gq_stats));
+  return GQ_OK;
+}
+
+int gq_get_statuses(const gq_batch* b, int32_t* status, int32_t* iters) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (status == nullptr) return fail(GQ_ERR_ARG, "status is NULL");
+  if (b->host_sol == nullptr) return fail(GQ_ERR_STATE, "host_sol not attached");
+  const gq_stats* st = reinterpret_cast<const gq_stats*>(static_cast<const char*>(b->host_sol) + b->L.stats);
+  for (int q = 0; q < b->nqp; ++q) {
+    status[q] = st[q].status;
+    if (iters) iters[q] = st[q].iters;
+  }
   return GQ_OK;
 }
 

@@ -87,6 +87,8 @@ SIGNATURES = {
     "gq_set_box": (c_int, [c_void_p, c_int, c_int, P_int, P_double, P_double, P_int, P_double, P_double]),
     "gq_set_general": (c_int, [c_void_p, c_int, c_int, P_double, c_int, P_double, c_int, P_double, P_double]),
     "gq_set_guess": (c_int, [c_void_p, c_int, P_double, P_double, P_double, P_double]),
+    "gq_set_initial_state": (c_int, [c_void_p, c_int, P_double, c_int, P_double, c_int, P_double, P_double, c_int,
+                                     P_double, P_double, c_int, P_double, P_double]),
     "gq_copy_qp": (c_int, [c_void_p, c_int, c_void_p, c_int]),
     "gq_upload": (c_int, [c_void_p, c_void_p]),
     "gq_upload_sol": (c_int, [c_void_p, c_void_p]),
@@ -97,6 +99,7 @@ SIGNATURES = {
     "gq_solve_noalloc": (c_int, [c_void_p, ctypes.POINTER(IpmArg), c_void_p, c_void_p, c_void_p]),
     "gq_get_stage_sol": (c_int, [c_void_p, c_int, c_int, P_double, P_double, P_double, P_double, P_double]),
     "gq_get_stats": (c_int, [c_void_p, c_int, ctypes.POINTER(Stats)]),
+    "gq_get_statuses": (c_int, [c_void_p, P_int, P_int]),
     "gq_get_sol_offsets": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64)]),
     "gq_last_error": (ctypes.c_char_p, []),
     "gq_server_cfg_default": (c_int, [ctypes.POINTER(ServerCfg)]),

@@ -205,3 +205,54 @@ def test_server_create_validates_before_any_cuda_call(gqmod):
     assert lib.gq_server_poll(None, 0, ctypes.byref(info)) == gqmod.GQ_ERR_ARG
     assert lib.gq_server_submit(None, None, None) == gqmod.GQ_ERR_ARG
     assert lib.gq_server_destroy(None) == gqmod.GQ_ERR_ARG
+
+
+def _f(a):
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def test_set_initial_state_folds_x0_like_the_elimination(gqmod):
+    """gq_set_initial_state writes the same stage-0 data as eliminating x_0
+    by hand (b_0 = b + A x0, r_0 = r + S x0, general bounds minus C x0), and
+    re-applying it with another x0 gives the data of that x0."""
+    from paper_2003_02547_gb300 import workloads as W
+    from paper_2003_02547_gb300.batch import QpBatch
+    lib = gqmod.load()
+    P = ctypes.POINTER(ctypes.c_double)
+    qp = W.ragged_random_qp(3)
+    assert qp.ng(0) > 0
+    x_new = qp.x0 + 0.05
+    for x in (qp.x0, x_new):
+        ref = QpBatch([W.perturb_x0(qp, x) if x is x_new else qp], device=None)
+        got = QpBatch([qp], device=None)
+        A, S, C = _f(qp.A[1]), _f(qp.S_full), _f(qp.C0_full)
+        b0 = np.ascontiguousarray(qp.b[0] - qp.A[1] @ qp.x0)
+        r0 = np.ascontiguousarray(qp.r[0] - qp.S_full @ qp.x0)
+        lg0 = np.ascontiguousarray(qp.lg[0] + qp.C0_full @ qp.x0)
+        ug0 = np.ascontiguousarray(qp.ug[0] + qp.C0_full @ qp.x0)
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        rc = lib.gq_set_initial_state(got.h, 0, xx.ctypes.data_as(P), xx.size, A.ctypes.data_as(P), A.shape[0],
+                                      b0.ctypes.data_as(P), S.ctypes.data_as(P), S.shape[0], r0.ctypes.data_as(P),
+                                      C.ctypes.data_as(P), C.shape[0], lg0.ctypes.data_as(P), ug0.ctypes.data_as(P))
+        assert rc == 0, lib.gq_last_error().decode()
+        n = got.sizes.in_bytes // 8
+        a = got.host_in.view(np.float64, 0, n)
+        c = ref.host_in.view(np.float64, 0, n)
+        np.testing.assert_allclose(a, c, rtol=1e-13, atol=1e-13, equal_nan=True)
+    b = QpBatch([qp], device=None)
+    assert lib.gq_set_initial_state(b.h, 0, None, -1, None, 1, None, None, 1, None, None, 1, None, None) == \
+        gqmod.GQ_ERR_ARG
+
+
+def test_get_statuses_reads_every_qp(gqmod):
+    from paper_2003_02547_gb300 import workloads as W
+    from paper_2003_02547_gb300.batch import QpBatch
+    b = QpBatch([W.small_random_qp(i) for i in range(3)], device=None)
+    st = b.host_sol.view(np.int32, 0, 3 * 16)
+    for q in range(3):
+        st[16 * q] = q          # status
+        st[16 * q + 1] = 10 + q  # iters
+    out, it = np.full(3, -9, dtype=np.int32), np.full(3, -9, dtype=np.int32)
+    P = ctypes.POINTER(ctypes.c_int)
+    assert gqmod.load().gq_get_statuses(b.h, out.ctypes.data_as(P), it.ctypes.data_as(P)) == 0
+    assert out.tolist() == [0, 1, 2] and it.tolist() == [10, 11, 12]
