@@ -219,6 +219,32 @@ GQ_API int gq_set_initial_state(gq_batch* b, int qp, const double* x0, int nx0, 
  * setters once). */
 GQ_API int gq_copy_qp(gq_batch* dst, int dst_qp, const gq_batch* src, int src_qp);
 
+/* ---- schedule: which QPs run one per warp, block size of the rest ---- */
+typedef struct gq_schedule {
+    int32_t warp_max_nv;   /* QPs whose stages all have nu + nx and nx at most this run
+                              one per warp (0..32; 0: every QP in the block kernel)   */
+    int32_t block_threads; /* threads per block of the block kernel: 64, 128 or 256    */
+    int32_t warp_qps;      /* out: QPs in the warp bucket                             */
+    int32_t block_qps;     /* out: QPs in the block bucket                            */
+} gq_schedule;
+
+/* Defaults: warp_max_nv 32, block_threads 256. */
+GQ_API int gq_get_schedule(const gq_batch* b, gq_schedule* out);
+
+/* Re-plans the buckets (host handle and host "in" staging); gq_upload before
+ * the next solve.  A different schedule may change the last bits of a QP's
+ * result (another summation split), never its accuracy.  Errors: GQ_ERR_ARG. */
+GQ_API int gq_set_schedule(gq_batch* b, const gq_schedule* sch);
+
+/* Autotuner: times `reps` solves of the batch (inputs attached, solution
+ * buffers overwritten) under each candidate schedule -- one QP per warp for
+ * small QPs or one block per QP for all, 256 or 128 threads per block --
+ * keeps the fastest, uploads it and returns it (and its mean solve time in
+ * ms).  Blocks until the timing solves finish (it synchronises `stream`).
+ * Errors: as gq_solve, GQ_ERR_CUDA for event failures. */
+GQ_API int gq_autotune(gq_batch* b, const gq_ipm_arg* arg, void* stream, int reps, gq_schedule* best,
+                       double* best_ms);
+
 /* ---- transfers (asynchronous on `stream`, a cudaStream_t; NULL = legacy) ---- */
 GQ_API int gq_upload(gq_batch* b, void* stream);       /* host_in  -> dev_in  */
 GQ_API int gq_upload_sol(gq_batch* b, void* stream);   /* host_sol -> dev_sol */

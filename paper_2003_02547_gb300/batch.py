@@ -201,6 +201,24 @@ class QpBatch:
         gq.check(self.lib.gq_newton_step(self.h, ctypes.byref(arg), float(sigma_mu), dev_dir.data_ptr(),
                                          self.stream_ptr(stream)))
 
+    # ---------------- schedule ----------------
+    def schedule(self) -> gq.Schedule:
+        sch = gq.Schedule()
+        gq.check(self.lib.gq_get_schedule(self.h, ctypes.byref(sch)))
+        return sch
+
+    def set_schedule(self, warp_max_nv: int, block_threads: int = 256) -> None:
+        sch = gq.Schedule(warp_max_nv, block_threads, 0, 0)
+        gq.check(self.lib.gq_set_schedule(self.h, ctypes.byref(sch)))
+
+    def autotune(self, arg: gq.IpmArg, reps: int = 2, stream=None):
+        """Pick the fastest schedule by timing solves; returns (schedule, ms)."""
+        sch = gq.Schedule()
+        ms = ctypes.c_double()
+        gq.check(self.lib.gq_autotune(self.h, ctypes.byref(arg), self.stream_ptr(stream), int(reps),
+                                      ctypes.byref(sch), ctypes.byref(ms)))
+        return sch, ms.value
+
     # ---------------- results ----------------
     def stats(self, i: int) -> gq.Stats:
         s = gq.Stats()

@@ -180,6 +180,60 @@ int gq_ipm_arg_default(gq_ipm_arg* arg, int mode, int precision) {
   return GQ_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Shape of the QPs at positions [lo, hi) of the order array (all QPs when
+// `all`, whatever the order).
+Shape bucket_shape(const gq_batch* b, int lo, int hi, bool all) {
+  Shape sh;
+  std::memset(&sh, 0, sizeof(sh));
+  for (int k = lo; k < hi; ++k) {
+    const QpDesc& d = b->qp[all ? k : b->order[k]];
+    sh.nst_max = std::max(sh.nst_max, d.N + 1);
+    sh.nside_max = std::max(sh.nside_max, d.nsidet);
+    for (int n = 0; n <= d.N; ++n) {
+      const StageDesc& st = b->st[d.stage0 + n];
+      const int nv = st.nx + st.nu;
+      sh.nvmax = std::max(sh.nvmax, nv);
+      sh.nxmax = std::max(sh.nxmax, st.nx);
+      sh.ngmax = std::max(sh.ngmax, st.ng);
+      sh.ne_max = std::max(sh.ne_max, n == 0 ? nv : st.nu);
+      sh.data_max = std::max(sh.data_max, stage_data_layout(st.nx, st.nu, st.nx1, st.nbu + st.nbx, st.ng).size);
+    }
+  }
+  return sh;
+}
+
+// Buckets under the batch's schedule: QPs whose stages fit one warp
+// (nu + nx and nx at most warp_max_nv) first, then the rest; each bucket in
+// longest-processing-time order (most expensive QPs launch first).
+void plan_buckets(gq_batch* b) {
+  const int nqp = b->nqp;
+  const QpDesc* qd = b->qp;
+  const int wmax = b->warp_max_nv;
+  auto warp_ok = [&](int q) { return qd[q].nvmax <= wmax && qd[q].nxmax <= wmax; };
+  int nw = 0;
+  for (int q = 0; q < nqp; ++q)
+    if (warp_ok(q)) b->order[nw++] = q;
+  int nb = nw;
+  for (int q = 0; q < nqp; ++q)
+    if (!warp_ok(q)) b->order[nb++] = q;
+  auto by_cost = [qd](int32_t a, int32_t c2) { return qd[a].cost > qd[c2].cost; };
+  std::stable_sort(b->order, b->order + nw, by_cost);
+  std::stable_sort(b->order + nw, b->order + nqp, by_cost);
+  b->nwarp = nw;
+  b->shape_w = bucket_shape(b, 0, nw, false);
+  b->shape_b = bucket_shape(b, nw, nqp, false);
+  if (nqp > nw) b->shape_b.mat_global = 1;
+  b->shape_b.threads = b->block_threads;
+}
+
+}  // namespace
+
+extern "C" {
+
 size_t gq_batch_memsize(int nqp, const int* dims, size_t dims_len, const int* stage_slot) {
   (void)stage_slot;
   Counts c = count_stages(nqp, dims, dims_len);
@@ -297,48 +351,17 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
   if (var >= INT32_MAX || eq >= INT32_MAX || side >= INT32_MAX)
     return fail(GQ_ERR_DIMS, "batch too large for 32-bit vector offsets");
 
-  // buckets: QPs whose stages fit one warp first, then the rest; each bucket
-  // in longest-processing-time order (most expensive QPs launch first)
-  QpDesc* qd = b->qp;
-  auto warp_ok = [&](int q) { return qd[q].nvmax <= kWarpMaxNv && qd[q].nxmax <= kWarpMaxNv; };
-  int nw = 0;
-  for (int q = 0; q < nqp; ++q)
-    if (warp_ok(q)) b->order[nw++] = q;
-  int nb_ = nw;
-  for (int q = 0; q < nqp; ++q)
-    if (!warp_ok(q)) b->order[nb_++] = q;
-  auto by_cost = [qd](int32_t a, int32_t c2) { return qd[a].cost > qd[c2].cost; };
-  std::stable_sort(b->order, b->order + nw, by_cost);
-  std::stable_sort(b->order + nw, b->order + nqp, by_cost);
-  b->nwarp = nw;
-  for (int bucket = 0; bucket < 2; ++bucket) {
-    Shape& sh = bucket == 0 ? b->shape_w : b->shape_b;
-    std::memset(&sh, 0, sizeof(sh));
-    const int lo = bucket == 0 ? 0 : nw, hi = bucket == 0 ? nw : nqp;
-    for (int k = lo; k < hi; ++k) {
-      const QpDesc& d = qd[b->order[k]];
-      sh.nst_max = std::max(sh.nst_max, d.N + 1);
-      sh.nside_max = std::max(sh.nside_max, d.nsidet);
-      for (int n = 0; n <= d.N; ++n) {
-        const StageDesc& st = b->st[d.stage0 + n];
-        const int nv = st.nx + st.nu;
-        sh.nvmax = std::max(sh.nvmax, nv);
-        sh.nxmax = std::max(sh.nxmax, st.nx);
-        sh.ngmax = std::max(sh.ngmax, st.ng);
-        sh.ne_max = std::max(sh.ne_max, n == 0 ? nv : st.nu);
-        sh.data_max = std::max(sh.data_max, stage_data_layout(st.nx, st.nu, st.nx1, st.nbu + st.nbx, st.ng).size);
-      }
-    }
-  }
-
+  b->warp_max_nv = kWarpMaxNv;
+  b->block_threads = 256;
+  plan_buckets(b);
   // the block kernel keeps its stage matrices in a per-QP slice of a global
   // scratch region (read through L1/L2): shared memory then holds only
   // vectors and the stage ring, so two blocks of 256 threads fit an SM.  On
   // the ragged workload this ran 1.5x faster than matrices in shared memory
   // at one block per SM (measured), and it is the only layout for stages
-  // whose matrices exceed shared memory.
-  if (nqp > nw) b->shape_b.mat_global = 1;
-  const int64_t matg_elems = b->shape_b.mat_global ? (int64_t)(nqp - nw) * block_mat_elems(b->shape_b) : 0;
+  // whose matrices exceed shared memory.  The scratch is sized for every QP
+  // in the block bucket, so that any schedule (gq_set_schedule) fits it.
+  const int64_t matg_elems = (int64_t)nqp * block_mat_elems(bucket_shape(b, 0, nqp, true));
 
   Layout& L = b->L;
   int64_t o = 0;
@@ -728,6 +751,92 @@ int gq_solve(gq_batch* b, const gq_ipm_arg* arg, void* stream) {
   if (rc) return rc;
   cudaError_t e = launch_all(b, k, *arg, static_cast<cudaStream_t>(stream), LaunchKind::Solve, 0.0, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "solve launch");
+  return GQ_OK;
+}
+
+int gq_get_schedule(const gq_batch* b, gq_schedule* out) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (out == nullptr) return fail(GQ_ERR_ARG, "out is NULL");
+  out->warp_max_nv = b->warp_max_nv;
+  out->block_threads = b->block_threads;
+  out->warp_qps = b->nwarp;
+  out->block_qps = b->nqp - b->nwarp;
+  return GQ_OK;
+}
+
+int gq_set_schedule(gq_batch* b, const gq_schedule* sch) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (sch == nullptr) return fail(GQ_ERR_ARG, "schedule is NULL");
+  if (sch->warp_max_nv < 0 || sch->warp_max_nv > kWarpMaxNv)
+    return fail(GQ_ERR_ARG, "warp_max_nv must be in 0..%d", kWarpMaxNv);
+  if (sch->block_threads != 64 && sch->block_threads != 128 && sch->block_threads != 256)
+    return fail(GQ_ERR_ARG, "block_threads must be 64, 128 or 256");
+  b->warp_max_nv = sch->warp_max_nv;
+  b->block_threads = sch->block_threads;
+  plan_buckets(b);
+  if (b->host_in)
+    std::memcpy(static_cast<char*>(b->host_in) + b->L.order, b->order, (size_t)b->nqp * sizeof(int32_t));
+  return GQ_OK;
+}
+
+int gq_autotune(gq_batch* b, const gq_ipm_arg* arg, void* stream, int reps, gq_schedule* best, double* best_ms) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  rc = check_arg(arg);
+  if (rc) return rc;
+  if (reps < 1 || reps > 100) return fail(GQ_ERR_ARG, "reps must be in 1..100");
+  if (!b->host_in) return fail(GQ_ERR_STATE, "host_in not attached");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const gq_schedule cands[] = {{kWarpMaxNv, 256, 0, 0}, {kWarpMaxNv, 128, 0, 0}, {0, 256, 0, 0}, {0, 128, 0, 0}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  double tbest = -1.0;
+  gq_schedule sbest = cands[0];
+  int seen_nwarp[4], seen_threads[4], nseen = 0;
+  for (const gq_schedule& c : cands) {
+    if (e != cudaSuccess) break;
+    gq_schedule probe = c;
+    rc = gq_set_schedule(b, &probe);
+    if (rc) break;
+    // a candidate that runs the same kernels as an earlier one is skipped
+    // (block size without block-bucket QPs)
+    const int thr = b->nqp > b->nwarp ? b->block_threads : 0;
+    bool dup = false;
+    for (int k = 0; k < nseen; ++k) dup = dup || (seen_nwarp[k] == b->nwarp && seen_threads[k] == thr);
+    if (dup) continue;
+    seen_nwarp[nseen] = b->nwarp;
+    seen_threads[nseen++] = thr;
+    rc = gq_upload(b, stream);
+    if (rc) break;
+    rc = gq_solve(b, arg, stream);  // warm-up
+    if (rc) break;
+    e = cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && e == cudaSuccess && rc == GQ_OK; ++r) rc = gq_solve(b, arg, stream);
+    if (rc) break;
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) break;
+    const double per = (double)ms / reps;
+    if (tbest < 0.0 || per < tbest) {
+      tbest = per;
+      sbest = c;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  if (rc) return rc;
+  rc = gq_set_schedule(b, &sbest);
+  if (rc) return rc;
+  rc = gq_upload(b, stream);
+  if (rc) return rc;
+  if (best) gq_get_schedule(b, best);
+  if (best_ms) *best_ms = tbest;
   return GQ_OK;
 }
 

@@ -1305,10 +1305,11 @@ cudaError_t launch_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, c
     cudaError_t e = cudaFuncSetAttribute(ipm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  // 256 threads whatever the stage size: the micro-tiled products and the
-  // trailing Cholesky updates have work for all of them (measured faster
-  // than one thread per stage row on the ragged and large-stage workloads)
-  const int nt = 256;
+  // 256 threads by default whatever the stage size: the micro-tiled products
+  // and the trailing Cholesky updates have work for all of them (measured
+  // faster than one thread per stage row on the ragged and large-stage
+  // workloads); the schedule may choose 64 or 128
+  const int nt = sh.threads > 0 ? sh.threads : 256;
   DirOut o{};
   if (out) o = *out;
   ipm_kernel<<<count, nt, smem, stream>>>(b, sh, arg, (int)kind, sigma_mu, o, order);

@@ -22,7 +22,7 @@ struct Shape {
   int nvmax, nxmax, ngmax;
   int64_t data_max;  // largest stage data block (elements)
   int32_t mat_global;  // block kernel: stage matrices in the global workspace (too large for shared memory)
-  int32_t pad;
+  int32_t threads;     // block kernel: threads per block (0: 256)
 };
 
 // Column width of the block kernel's Cholesky panels.

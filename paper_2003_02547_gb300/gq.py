@@ -49,6 +49,11 @@ class Sizes(ctypes.Structure):
                 ("nx_max", ctypes.c_int32)]
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("warp_max_nv", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("warp_qps", ctypes.c_int32), ("block_qps", ctypes.c_int32)]
+
+
 class ServerCfg(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("max_wait_us", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("cache_bytes", c_size_t), ("arg", IpmArg),
@@ -90,6 +95,10 @@ SIGNATURES = {
     "gq_set_initial_state": (c_int, [c_void_p, c_int, P_double, c_int, P_double, c_int, P_double, P_double, c_int,
                                      P_double, P_double, c_int, P_double, P_double]),
     "gq_copy_qp": (c_int, [c_void_p, c_int, c_void_p, c_int]),
+    "gq_get_schedule": (c_int, [c_void_p, ctypes.POINTER(Schedule)]),
+    "gq_set_schedule": (c_int, [c_void_p, ctypes.POINTER(Schedule)]),
+    "gq_autotune": (c_int, [c_void_p, ctypes.POINTER(IpmArg), c_void_p, c_int, ctypes.POINTER(Schedule),
+                            ctypes.POINTER(c_double)]),
     "gq_upload": (c_int, [c_void_p, c_void_p]),
     "gq_upload_sol": (c_int, [c_void_p, c_void_p]),
     "gq_download": (c_int, [c_void_p, c_void_p]),

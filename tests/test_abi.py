@@ -256,3 +256,23 @@ def test_get_statuses_reads_every_qp(gqmod):
     P = ctypes.POINTER(ctypes.c_int)
     assert gqmod.load().gq_get_statuses(b.h, out.ctypes.data_as(P), it.ctypes.data_as(P)) == 0
     assert out.tolist() == [0, 1, 2] and it.tolist() == [10, 11, 12]
+
+
+def test_schedule_replans_buckets(gqmod):
+    from paper_2003_02547_gb300 import workloads as W
+    from paper_2003_02547_gb300.batch import QpBatch
+    qps = [W.small_random_qp(0), W.ragged_random_qp(0), W.mass_spring_qp(0)]
+    b = QpBatch(qps, device=None)
+    sch = b.schedule()
+    assert (sch.warp_max_nv, sch.block_threads) == (32, 256)
+    nw = sum(max(q.nx[n] + q.nu[n] for n in range(q.N + 1)) <= 32 and max(q.nx) <= 32 for q in qps)
+    assert (sch.warp_qps, sch.block_qps) == (nw, len(qps) - nw)
+    b.set_schedule(0, 128)
+    sch = b.schedule()
+    assert (sch.warp_qps, sch.block_qps, sch.block_threads) == (0, 3, 128)
+    lib = gqmod.load()
+    bad = gqmod.Schedule(33, 256, 0, 0)
+    assert lib.gq_set_schedule(b.h, ctypes.byref(bad)) == gqmod.GQ_ERR_ARG
+    bad = gqmod.Schedule(32, 96, 0, 0)
+    assert lib.gq_set_schedule(b.h, ctypes.byref(bad)) == gqmod.GQ_ERR_ARG
+

@@ -323,3 +323,37 @@ def test_mass_spring_full_batch(env, precision):
         # the FP32 factors plus refinement suffice on this workload: a QP
         # handed to FP64 would mean inaccurate FP32 factors
         assert not np.any(b.all_stats()["flags"] & 1)
+
+
+def test_schedules_agree_and_autotune_picks_one(env):
+    """The same QPs solved one per warp and one per block (two different
+    kernels) meet the same oracle gates; the autotuner returns one of its
+    candidate schedules and leaves the batch solving correctly."""
+    gq, QpBatch, torch = env
+    qps = [W.mass_spring_qp(i) for i in range(3)] + [W.small_random_qp(1)]
+    refs = [oracle_pair(q) for q in qps]
+    for prec in (1, 0):
+        arg = gq.default_arg(0, prec)
+        sols = []
+        for wmax, thr in ((32, 256), (0, 256), (0, 128)):
+            b = QpBatch(qps)
+            b.set_schedule(wmax, thr)
+            b.upload()
+            b.solve(arg)
+            b.download()
+            torch.cuda.synchronize()
+            sch = b.schedule()
+            assert sch.warp_qps == (len(qps) if wmax else 0)
+            _check_converged(b, qps, refs)
+            sols.append([b.solution(i)[0] for i in range(len(qps))])
+        for other in sols[1:]:
+            for y0, y1 in zip(sols[0], other):
+                assert rel_err(y1, y0) <= 1e-6
+        b = QpBatch(qps)
+        b.upload()
+        sch, ms = b.autotune(arg, reps=2)
+        assert (sch.warp_max_nv, sch.block_threads) in ((32, 256), (32, 128), (0, 256), (0, 128)) and ms > 0
+        b.solve(arg)
+        b.download()
+        torch.cuda.synchronize()
+        _check_converged(b, qps, refs)
