@@ -233,10 +233,11 @@ def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: in
     }
 
 
-def single_qp_latency(dev, precision: int, solves: int = 10000):
+def single_qp_latency(dev, precision: int, solves: int = 10000, graph: bool = False):
     """The single small QP (N=10, nx=4, nu=2) solved alone, back to back,
     one solve call at a time with its launches included: per-solve latency
-    percentiles from CUDA events around each call."""
+    percentiles from CUDA events around each call.  With `graph`, one solve
+    call is captured in a CUDA graph and each solve is a graph replay."""
     import numpy as np
     import torch
     from paper_2003_02547_gb300 import gq, workloads as W
@@ -247,10 +248,19 @@ def single_qp_latency(dev, precision: int, solves: int = 10000):
     for _ in range(20):
         b.solve(arg)
     torch.cuda.synchronize()
+    run = lambda: b.solve(arg)
+    if graph:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            b.solve(arg)
+        run = g.replay
+        for _ in range(20):
+            run()
+        torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(solves)]
     for e0, e1 in evs:
         e0.record()
-        b.solve(arg)
+        run()
         e1.record()
     torch.cuda.synchronize()
     ms = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
@@ -295,7 +305,7 @@ def batch_run(qps, dev, precision: int, reps: int = 2):
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; summary in
 # profiles/).  It is reported only while the kernel sources hash to the
 # value recorded with the capture; after any change it reads null.
-TRAFFIC_CAPTURE = {"sha256": "9cafd5d003241bd61089ad37c1137bea0a29a00352db829cea3a3ca974e8ae50", "bytes": 6033957000}
+TRAFFIC_CAPTURE = {"sha256": "29b6cd028ad3062ee804bc80df26a31f25b7cc4979b9e30963bb7f64529e892a", "bytes": 6030026000}
 KERNEL_SOURCES = ["gq_warp.cu", "gq_device.h", "gq_internal.h", "gq_launch.h", "gq_mma.h"]
 
 
@@ -489,6 +499,7 @@ def main():
         del singles
         extras["single_small_qp_mixed"] = single_qp_latency(dev, gq.PREC_MIXED)
         extras["single_small_qp_fp64"] = single_qp_latency(dev, gq.PREC_FP64)
+        extras["single_small_qp_mixed_graph"] = single_qp_latency(dev, gq.PREC_MIXED, graph=True)
         ragged = W.ragged_batch(4096)
         extras["ragged_4096_mixed"] = batch_run(ragged, dev, gq.PREC_MIXED)
         extras["ragged_4096_fp64"] = batch_run(ragged, dev, gq.PREC_FP64)

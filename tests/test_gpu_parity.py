@@ -357,3 +357,27 @@ def test_schedules_agree_and_autotune_picks_one(env):
         b.download()
         torch.cuda.synchronize()
         _check_converged(b, qps, refs)
+
+
+def test_solve_replays_from_a_cuda_graph(env):
+    """A solve call (mirror copy, FP32 launch, FP64 continuation launch) is
+    captured in a CUDA graph; each replay gives the bits of a direct solve."""
+    gq, QpBatch, torch = env
+    qps = [W.small_random_qp(0), W.mass_spring_qp(3)]
+    arg = gq.default_arg(0, 1)
+    ref = solve_gpu(env, qps, precision=1)
+    b = QpBatch(qps)
+    b.upload()
+    b.solve(arg)          # first call outside the capture (launch attributes)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.solve(arg)
+    for _ in range(3):
+        b.dev_sol.zero_()
+        g.replay()
+    b.download()
+    torch.cuda.synchronize()
+    for i in range(len(qps)):
+        for a, c in zip(ref.solution(i), b.solution(i)):
+            np.testing.assert_array_equal(a, c)
