@@ -276,3 +276,19 @@ def test_schedule_replans_buckets(gqmod):
     bad = gqmod.Schedule(32, 96, 0, 0)
     assert lib.gq_set_schedule(b.h, ctypes.byref(bad)) == gqmod.GQ_ERR_ARG
 
+
+
+def test_copy_qp_moves_stage_data_between_batches(gqmod):
+    """gq_copy_qp copies every stage block of a QP into another batch's QP of
+    the same sizes; other sizes are refused with GQ_ERR_DIMS."""
+    from paper_2003_02547_gb300 import workloads as W
+    from paper_2003_02547_gb300.batch import QpBatch
+    lib = gqmod.load()
+    src = QpBatch([W.small_random_qp(4), W.ragged_random_qp(2)], device=None)
+    dst = QpBatch([W.ragged_random_qp(2), W.small_random_qp(9)], device=None, set_data=False)
+    assert lib.gq_copy_qp(dst.h, 0, src.h, 1) == 0
+    assert lib.gq_copy_qp(dst.h, 1, src.h, 0) == 0
+    ref = QpBatch([W.ragged_random_qp(2), W.small_random_qp(4)], device=None)
+    n = ref.sizes.in_bytes // 8
+    np.testing.assert_array_equal(dst.host_in.view(np.uint8, 0, n * 8), ref.host_in.view(np.uint8, 0, n * 8))
+    assert lib.gq_copy_qp(dst.h, 0, src.h, 0) == gqmod.GQ_ERR_DIMS
