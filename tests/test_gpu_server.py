@@ -200,3 +200,30 @@ def test_size_classes_group_micro_batches(env, class_ratio):
         assert all(sz == (3 if b else 6) for sz, b in zip(sizes, is_big)), sizes
     else:
         assert all(sz == 9 for sz in sizes), sizes
+
+
+
+def test_bad_requests_and_shutdown_fail_cleanly(env):
+    """A request for a QP index outside its source is refused at submit, and
+    destroying a server with requests still queued returns promptly (the
+    micro-batch in flight finishes, the rest are dropped) and leaves the GPU
+    usable."""
+    import time
+    gq, server, QpBatch, torch = env
+    qps = [W.ragged_random_qp(i) for i in range(6)]
+    src = QpBatch(qps, device=None)
+    srv = server.Server(1 << 28, lanes=1, max_batch=1, max_wait_us=0)
+    with pytest.raises(gq.GqError) as e:
+        srv.submit(src, 17)
+    assert e.value.code == gq.GQ_ERR_ARG
+    for i in range(6):
+        srv.submit(src, i)
+    t0 = time.monotonic()
+    srv.close()
+    assert time.monotonic() - t0 < 30.0
+    b = QpBatch([W.small_random_qp(0)])
+    b.upload()
+    b.solve(gq.default_arg(0, 1))
+    b.download()
+    torch.cuda.synchronize()
+    assert b.all_stats()["status"][0] == gq.STATUS_CONVERGED
