@@ -99,7 +99,12 @@ typedef struct gq_ipm_arg {
     int32_t ir_steps;      /* max iterative-refinement steps per direction (3.4)   */
     int32_t cond_corr;     /* 1: conditional Mehrotra corrector (Sec. 4.2)         */
     int32_t fp64_fallback; /* mixed path: 1 = refactor in FP64 when IR stagnates   */
-    int32_t reserved0;
+    int32_t riccati;       /* 0 square-root Riccati (Sec. 3.3, variant b: needs every
+                              stage Hessian plus barrier terms positive definite);
+                              1 classical Riccati (variant a: only the reduced
+                              Hessians R + B'PB positive definite, so an indefinite
+                              Q is allowed); the classical form runs in the block
+                              kernel only (schedule warp_max_nv = 0)                */
     double tol_stat;       /* exit: ||r_g||inf <= tol_stat                          */
     double tol_eq;         /*       ||r_b||inf <= tol_eq                            */
     double tol_ineq;       /*       ||r_d||inf <= tol_ineq                          */

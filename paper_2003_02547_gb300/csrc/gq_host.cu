@@ -675,6 +675,16 @@ int gq_download(gq_batch* b, void* stream) {
   return copy(b->host_sol, b->dev_sol, b->sizes.sol_bytes, cudaMemcpyDeviceToHost, stream, "download");
 }
 
+// the classical Riccati variant is implemented in the block kernel only
+static int check_variant(const gq_batch* b, const gq_ipm_arg* a) {
+  if (a->riccati == 1 && b->nwarp > 0)
+    return fail(GQ_ERR_ARG,
+                "classical Riccati runs in the block kernel: set the schedule's warp_max_nv to 0 "
+                "(%d QPs are in the warp bucket)",
+                b->nwarp);
+  return GQ_OK;
+}
+
 static int make_kernel_batch(gq_batch* b, Batch* k) {
   if (!b->dev_in || !b->dev_sol || !b->dev_ws) return fail(GQ_ERR_STATE, "device buffers not attached");
   char* in = static_cast<char*>(b->dev_in);
@@ -734,6 +744,7 @@ static int check_arg(const gq_ipm_arg* a) {
   if (a->precision != GQ_PREC_FP64 && a->precision != GQ_PREC_MIXED) return fail(GQ_ERR_ARG, "unknown precision");
   if (a->iter_max < 0 || a->ir_steps < 0 || a->ir_steps > 64) return fail(GQ_ERR_ARG, "iter_max/ir_steps out of range");
   if (a->warm_start < 0 || a->warm_start > 2) return fail(GQ_ERR_ARG, "warm_start must be 0, 1 or 2");
+  if (a->riccati != 0 && a->riccati != 1) return fail(GQ_ERR_ARG, "riccati must be 0 (square-root) or 1 (classical)");
   if (!(a->tau_b > 0.0 && a->tau_b <= 1.0)) return fail(GQ_ERR_ARG, "tau_b must be in (0, 1]");
   if (!(a->lam_min > 0.0 && a->t_min > 0.0)) return fail(GQ_ERR_ARG, "lam_min and t_min must be positive");
   if (!(a->reg_prim >= 0.0)) return fail(GQ_ERR_ARG, "reg_prim must be >= 0");
@@ -745,6 +756,8 @@ int gq_solve(gq_batch* b, const gq_ipm_arg* arg, void* stream) {
   int rc = check_batch(b);
   if (rc) return rc;
   rc = check_arg(arg);
+  if (rc) return rc;
+  rc = check_variant(b, arg);
   if (rc) return rc;
   Batch k;
   rc = make_kernel_batch(b, &k);
@@ -857,6 +870,8 @@ int gq_newton_step(gq_batch* b, const gq_ipm_arg* arg, double sigma_mu, void* de
   int rc = check_batch(b);
   if (rc) return rc;
   rc = check_arg(arg);
+  if (rc) return rc;
+  rc = check_variant(b, arg);
   if (rc) return rc;
   if (dev_dir == nullptr || reinterpret_cast<uintptr_t>(dev_dir) % 256)
     return fail(GQ_ERR_ARG, "dev_dir must be non-NULL and 256-byte aligned");
@@ -981,6 +996,8 @@ extern "C" int gq_solve_noalloc(gq_batch* b, const gq_ipm_arg* arg, void* dev_in
   int rc = check_batch(b);
   if (rc) return rc;
   rc = check_arg(arg);
+  if (rc) return rc;
+  rc = check_variant(b, arg);
   if (rc) return rc;
   if (dev_in == nullptr || dev_sol == nullptr) return fail(GQ_ERR_ARG, "noalloc: dev_in and dev_sol must be non-NULL");
   if (reinterpret_cast<uintptr_t>(dev_in) % 256 || reinterpret_cast<uintptr_t>(dev_sol) % 256)

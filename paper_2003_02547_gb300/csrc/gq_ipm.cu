@@ -137,6 +137,7 @@ struct Ctx {
   void* panel;  // shared-memory copy of one Cholesky column panel (nv x kBlockPanel, Tf)
   void* mat;  // matrix scratch (Tf): L_{n+1}, Phi, M
   int nvmax, nxmax;
+  bool classical;  // classical Riccati: explicit P_{n+1} in place of L_{n+1}
   Ring ring;
 };
 
@@ -442,7 +443,7 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
       for (int u = w; u < nMT * nNG; u += NW) {
         const int mt = u / nNG, nt0 = (u - mt * nNG) * 4;
         float c[4][4] = {};
-        for (int kt = nt0; kt * 8 < nx1; ++kt) {
+        for (int kt = C.classical ? 0 : nt0; kt * 8 < nx1; ++kt) {
           auto fa = [&](int r, int k) {
             const int ii = mt * 16 + r, kk = kt * 8 + k;
             return (ii < nv && kk < nx1) ? (float)D[L.BAt + (int64_t)ii * L.ldb + kk] : 0.f;
@@ -453,7 +454,7 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
 #pragma unroll
           for (int jn = 0; jn < 4; ++jn) {
             const int nt = nt0 + jn;
-            if (nt >= nNT || kt < nt) continue;
+            if (nt >= nNT || (kt < nt && !C.classical)) continue;
             auto fb = [&](int k, int j) {
               const int kk = kt * 8 + k, jj = nt * 8 + j;
               return (kk < nx1 && jj < nx1) ? (float)sL[kk * nx1 + jj] : 0.f;
@@ -503,7 +504,12 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
           for (int jn = 0; jn < 4; ++jn) {
             const int nt = nt0 + jn;
             if (nt >= nNT || nt * 8 > mt * 16 + 15) continue;
-            const Tf32Pair b0 = tf32_split(val(nt * 8 + g, kt * 8 + q)), b1 = tf32_split(val(nt * 8 + g, kt * 8 + q + 4));
+            // B = M' (square-root: M M'), or [B A] rows (classical: M [B A]' = [B A]' P [B A])
+            auto fbv = [&](int j, int k) -> float {
+              if (C.classical && k < kend) return j < nv ? (float)D[L.BAt + (int64_t)j * L.ldb + k] : 0.f;
+              return val(j, k);
+            };
+            const Tf32Pair b0 = tf32_split(fbv(nt * 8 + g, kt * 8 + q)), b1 = tf32_split(fbv(nt * 8 + g, kt * 8 + q + 4));
             const uint32_t bhi[2] = {b0.hi, b1.hi}, blo[2] = {b0.lo, b1.lo};
             mma_tf32(c[jn], alo, bhi);
             mma_tf32(c[jn], ahi, blo);
@@ -538,7 +544,7 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
         const double* ba[kT];
   #pragma unroll
         for (int r = 0; r < kT; ++r) ba[r] = D + L.BAt + (int64_t)min(I * kT + r, nv - 1) * L.ldb;
-        for (int k = J * kT; k < nx1; ++k) {
+        for (int k = C.classical ? 0 : J * kT; k < nx1; ++k) {
           Tf a[kT], bb[kT];
   #pragma unroll
           for (int r = 0; r < kT; ++r) a[r] = (Tf)ba[r][k];
@@ -596,7 +602,8 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
   #pragma unroll
           for (int r = 0; r < kT; ++r) a[r] = mk[min(I * kT + r, nv - 1)];
   #pragma unroll
-          for (int c = 0; c < kT; ++c) bb[c] = mk[min(J * kT + c, nv - 1)];
+          for (int c = 0; c < kT; ++c)
+            bb[c] = C.classical ? (Tf)D[L.BAt + (int64_t)min(J * kT + c, nv - 1) * L.ldb + k] : mk[min(J * kT + c, nv - 1)];
   #pragma unroll
           for (int r = 0; r < kT; ++r)
   #pragma unroll
@@ -628,8 +635,11 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
   // threads in kT x kT tiles read from the shared copy
   const int lane = tid & 31;
   Tf* sPan = static_cast<Tf*>(C.panel);  // rows p0..nv-1 of the panel, ld kPanel
-  for (int p0 = 0; p0 < nv; p0 += kPanel) {
-    const int pw = min(kPanel, nv - p0), pr = nv - p0;
+  // square-root: all nv columns; classical: the leading ne columns only, so
+  // the trailing block becomes the Schur complement P_n = Phi_kk - L_ke L_ke'
+  const int ncol = C.classical ? ne : nv;
+  for (int p0 = 0; p0 < ncol; p0 += kPanel) {
+    const int pw = min(kPanel, ncol - p0), pr = nv - p0;
     for (int e = tid; e < pr * kPanel; e += NT) {
       const int r = e / kPanel, c = e - r * kPanel;
       sPan[e] = c < pw ? sPhi[(p0 + r) * ldP + p0 + c] : (Tf)0;
@@ -719,9 +729,13 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
     const int i = e / nv, j = e - i * nv;
     F[e] = j > i ? (Tf)0 : (i < ne ? sMt[i * ne + j] : sPhi[i * ldP + j]);
   }
+  // next stage: L_n = L_kk (lower, zeros above), or P_n (full symmetric)
   for (int e = tid; e < nk * nk; e += NT) {
     const int i = e / nk, j = e - i * nk;
-    sL[i * nk + j] = (j <= i) ? sPhi[(ne + i) * ldP + ne + j] : (Tf)0;
+    if (C.classical)
+      sL[i * nk + j] = sPhi[(ne + max(i, j)) * ldP + ne + min(i, j)];
+    else
+      sL[i * nk + j] = (j <= i) ? sPhi[(ne + i) * ldP + ne + j] : (Tf)0;
   }
   return ok;
 }
@@ -776,7 +790,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
         vs[c] = v;
       }
     }
-    if (n < C.N) {
+    if (n < C.N && !C.classical) {
       // va = L_{n+1}' rb_n
       rows_dot<Tf>(
           nx1, [&](int k) { return k; }, [&](int) { return nx1; },
@@ -784,10 +798,17 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     }
     __syncthreads();
     if (n < C.N) {
-      // vb = L_{n+1} va + p_{n+1}
-      rows_dot<Tf>(
-          nx1, [&](int) { return 0; }, [&](int k) { return k + 1; },
-          [&](int k, int j) { return sL[k * nx1 + j] * va[j]; }, [&](int k, Tf v) { vb[k] = pn1[k] + v; });
+      if (C.classical) {
+        // vb = P_{n+1} rb_n + p_{n+1}
+        rows_dot<Tf>(
+            nx1, [&](int) { return 0; }, [&](int) { return nx1; },
+            [&](int k, int j) { return sL[k * nx1 + j] * (Tf)rb[s.eq + j]; }, [&](int k, Tf v) { vb[k] = pn1[k] + v; });
+      } else {
+        // vb = L_{n+1} va + p_{n+1}
+        rows_dot<Tf>(
+            nx1, [&](int) { return 0; }, [&](int k) { return k + 1; },
+            [&](int k, int j) { return sL[k * nx1 + j] * va[j]; }, [&](int k, Tf v) { vb[k] = pn1[k] + v; });
+      }
     }
     __syncthreads();
     // phi = gt_n + [B A]' vb
@@ -828,7 +849,8 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
         });
     for (int e = tid; e < nk * nk; e += NT) {
       const int i = e / nk, j = e - i * nk;
-      sL[i * nk + j] = F[(ne + i) * nv + ne + j];
+      // L_n (lower, zeros above) or P_n (stored lower, used full)
+      sL[i * nk + j] = C.classical ? F[(ne + max(i, j)) * nv + ne + min(i, j)] : F[(ne + i) * nv + ne + j];
     }
   });
   // forward sweep: pi_n at the start of stage n (needs L_n), then y_n and
@@ -841,17 +863,25 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     const int ne = elim_size(s, n), nk = nv - ne;
     double* yn = dy + s.var;
     if (n > 0) {
-      // pi_n = L_n (L_n' x_n) + p_n,  L_n = L_kk of this stage
       const double* xn = yn + ne;
-      rows_dot<Tf>(
-          nk, [&](int k) { return k; }, [&](int) { return nk; },
-          [&](int k, int j) { return F[(ne + j) * nv + ne + k] * (Tf)xn[j]; }, [&](int k, Tf v) { va[k] = v; });
-      __syncthreads();
       const int eqp = C.st[n - 1].eq;
-      rows_dot<Tf>(
-          nk, [&](int) { return 0; }, [&](int k) { return k + 1; },
-          [&](int k, int j) { return F[(ne + k) * nv + ne + j] * va[j]; },
-          [&](int k, Tf v) { dpi[eqp + k] = (double)((Tf)lp[s.var + ne + k] + v); });
+      if (C.classical) {
+        // pi_n = P_n x_n + p_n, P_n stored in the lower kk block
+        rows_dot<Tf>(
+            nk, [&](int) { return 0; }, [&](int) { return nk; },
+            [&](int k, int j) { return F[(ne + max(k, j)) * nv + ne + min(k, j)] * (Tf)xn[j]; },
+            [&](int k, Tf v) { dpi[eqp + k] = (double)((Tf)lp[s.var + ne + k] + v); });
+      } else {
+        // pi_n = L_n (L_n' x_n) + p_n,  L_n = L_kk of this stage
+        rows_dot<Tf>(
+            nk, [&](int k) { return k; }, [&](int) { return nk; },
+            [&](int k, int j) { return F[(ne + j) * nv + ne + k] * (Tf)xn[j]; }, [&](int k, Tf v) { va[k] = v; });
+        __syncthreads();
+        rows_dot<Tf>(
+            nk, [&](int) { return 0; }, [&](int k) { return k + 1; },
+            [&](int k, int j) { return F[(ne + k) * nv + ne + j] * va[j]; },
+            [&](int k, Tf v) { dpi[eqp + k] = (double)((Tf)lp[s.var + ne + k] + v); });
+      }
       __syncthreads();
     }
     // va = l + L_ke' x_n
@@ -1031,6 +1061,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
   C.ring.parity = 0;
   C.ring.fac_off = (uint32_t)P.ring_fac;
   C.ring.staged = P.staged;
+  C.classical = arg.riccati == 1;
   C.ring.ok = true;
 
   // count active sides (integer count: exact in any order)

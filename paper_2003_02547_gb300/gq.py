@@ -29,7 +29,7 @@ P_double = ctypes.POINTER(ctypes.c_double)
 class IpmArg(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("precision", ctypes.c_int32), ("iter_max", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("ir_steps", ctypes.c_int32), ("cond_corr", ctypes.c_int32),
-                ("fp64_fallback", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("fp64_fallback", ctypes.c_int32), ("riccati", ctypes.c_int32),
                 ("tol_stat", c_double), ("tol_eq", c_double), ("tol_ineq", c_double), ("tol_comp", c_double),
                 ("alpha_min", c_double), ("lam_min", c_double), ("t_min", c_double), ("tau_b", c_double),
                 ("corr_k", c_double), ("reg_prim", c_double), ("ir_tol", c_double), ("warm_min", c_double),

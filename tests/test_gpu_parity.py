@@ -381,3 +381,42 @@ def test_solve_replays_from_a_cuda_graph(env):
     for i in range(len(qps)):
         for a, c in zip(ref.solution(i), b.solution(i)):
             np.testing.assert_array_equal(a, c)
+
+
+def _solve_sched(env, qps, precision, riccati, wmax=0):
+    gq, QpBatch, torch = env
+    b = QpBatch(qps)
+    b.set_schedule(wmax, 256)
+    b.upload()
+    b.solve(gq.default_arg(0, precision, riccati=riccati))
+    b.download()
+    torch.cuda.synchronize()
+    return b
+
+
+def test_classical_riccati_solves_indefinite_state_cost(env):
+    """NEXT-1: with an indefinite Q (reduced Hessians positive definite) the
+    square-root factorisation has no Cholesky factor and the QP ends NaN;
+    the classical variant converges to the oracle's solution."""
+    gq, QpBatch, torch = env
+    qps = [P.indefinite_lq(s) for s in range(3)]
+    refs = [oracle_pair(q) for q in qps]
+    for prec in (0, 1):
+        sq = _solve_sched(env, qps, prec, 0)
+        assert np.all(sq.all_stats()["status"] == gq.STATUS_NAN)
+        cl = _solve_sched(env, qps, prec, 1)
+        _check_converged(cl, qps, refs)
+
+
+def test_classical_riccati_matches_square_root_on_convex_qps(env):
+    """On strictly convex QPs both variants reach the oracle's solution."""
+    gq, QpBatch, torch = env
+    qps = [W.small_random_qp(2), W.mass_spring_qp(4)] + mixed_set()[:2] + [W.ragged_random_qp(1)]
+    refs = [oracle_pair(q) for q in qps]
+    for prec in (0, 1):
+        cl = _solve_sched(env, qps, prec, 1)
+        _check_converged(cl, qps, refs)
+    b = QpBatch(qps)          # default schedule: warp bucket present
+    with pytest.raises(gq.GqError) as e:
+        b.solve(gq.default_arg(0, 0, riccati=1))
+    assert e.value.code == gq.GQ_ERR_ARG

@@ -439,3 +439,58 @@ def test_mass_spring_batch_converges():
     for i in range(3):
         res = O.solve(W.mass_spring_qp(i))
         assert res.status == O.CONVERGED, (i, res.res)
+
+
+def indefinite_lq(seed, N=8, nx=4, nu=2):
+    """An OCP QP with an indefinite state cost (one negative eigenvalue of Q)
+    whose reduced Hessians R + B'PB stay positive definite, x_0 eliminated,
+    box bounds far outside the solution (inactive)."""
+    from paper_2003_02547_gb300 import workloads as W
+    rng = np.random.default_rng([77, seed])
+    G = rng.standard_normal((nx, nx))
+    A = G * (0.9 / max(abs(np.linalg.eigvals(G))))
+    B = rng.standard_normal((nx, nu))
+    b = 0.1 * rng.standard_normal(nx)
+    Q = np.diag(np.r_[np.ones(nx - 1), -0.3])
+    R = 3.0 * np.eye(nu)
+    S = np.zeros((nu, nx))
+    q = 0.5 * rng.standard_normal(nx)
+    r = 0.5 * rng.standard_normal(nu)
+    x0 = rng.uniform(-1, 1, nx)
+    qp = W._assemble(N, A, B, b, Q, R, S, q, r, x0, 1e3, 1e3, name=f"indef{seed}")
+    qp.validate()
+    return qp
+
+
+def reduced_hessian_min_eig(qp):
+    """Smallest eigenvalue of R_n + B_n' P_{n+1} B_n over the stages of the
+    classical Riccati recursion (positive: the QP is strictly convex on the
+    dynamics)."""
+    P = qp.Q[qp.N].copy()
+    mn = np.inf
+    for n in range(qp.N - 1, -1, -1):
+        An, Bn = qp.A[n], qp.B[n]
+        Rb = qp.R[n] + Bn.T @ P @ Bn
+        Sb = qp.S[n] + Bn.T @ P @ An
+        Qb = qp.Q[n] + An.T @ P @ An
+        mn = min(mn, float(np.min(np.linalg.eigvalsh(Rb))))
+        P = Qb - Sb.T @ np.linalg.solve(Rb, Sb)
+    return mn
+
+
+def test_indefinite_state_cost_matches_riccati_dp():
+    """NEXT-1 pin: with Q indefinite but every reduced Hessian positive
+    definite, the oracle (pivoted LDL' of the full KKT system) reaches the
+    solution of the classical Riccati recursion; the stage Hessian of the last
+    stage alone is indefinite, so no square-root factorisation exists."""
+    for seed in range(3):
+        qp = indefinite_lq(seed)
+        assert reduced_hessian_min_eig(qp) > 0.1
+        assert np.min(np.linalg.eigvalsh(qp.Q[qp.N])) < 0
+        res = O.solve(qp)
+        assert res.status == O.CONVERGED
+        us, xs, pis = riccati_dp(qp)
+        st = O.split_stages(qp, res.dq, res.y)
+        for n in range(qp.N + 1):
+            np.testing.assert_allclose(st[n][0], us[n], rtol=1e-8, atol=1e-8)
+            np.testing.assert_allclose(st[n][1], xs[n], rtol=1e-8, atol=1e-8)
