@@ -271,6 +271,39 @@ def single_qp_latency(dev, precision: int, solves: int = 10000, graph: bool = Fa
             "solves_per_s": float(1e3 / ms.mean()), "iters": int(st["iters"][0]), "converged": int(st["status"][0] == 0)}
 
 
+def condensed_run(qps, block: int, dev, precision: int, reps: int = 3):
+    """The batch partially condensed by `block` stages (host, libgq) and solved
+    on the device; like the paper's timings the solve is timed alone, and
+    the host condensing time is reported beside it."""
+    import numpy as np
+    import torch
+    from paper_2003_02547_gb300 import condense as CD, gq
+    from paper_2003_02547_gb300.batch import QpBatch
+    src = QpBatch(qps, device=None)
+    t0 = time.perf_counter()
+    dst = CD.condense(src, range(len(qps)), block, device=dev)
+    t_cond = time.perf_counter() - t0
+    arg = gq.default_arg(gq.MODE_SPEED, precision)
+    dst.upload()
+    dst.solve(arg)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dst.solve(arg)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    dst.download()
+    torch.cuda.synchronize()
+    st = dst.all_stats()
+    sch = dst.schedule()
+    return {"block": block, "value": len(qps) / (min(ms) * 1e-3), "unit": UNIT, "ms": min(ms),
+            "host_condense_s": t_cond, "converged": int(np.sum(st["status"] == 0)),
+            "iters_mean": float(np.mean(st["iters"])), "warp_qps": int(sch.warp_qps), "block_qps": int(sch.block_qps)}
+
+
 def batch_run(qps, dev, precision: int, reps: int = 2):
     """Device-timed solves of one batch in one call (inputs resident)."""
     import numpy as np
@@ -497,6 +530,8 @@ def main():
     extras = {}
     if rank == 0 and world == 1 and not a.no_extras:
         del singles
+        extras["mass_spring_condensed_2_mixed"] = condensed_run(qps, 2, dev, gq.PREC_MIXED)
+        extras["mass_spring_condensed_3_mixed"] = condensed_run(qps, 3, dev, gq.PREC_MIXED)
         extras["single_small_qp_mixed"] = single_qp_latency(dev, gq.PREC_MIXED)
         extras["single_small_qp_fp64"] = single_qp_latency(dev, gq.PREC_FP64)
         extras["single_small_qp_mixed_graph"] = single_qp_latency(dev, gq.PREC_MIXED, graph=True)

@@ -203,6 +203,39 @@ GQ_API int gq_set_general(gq_batch* b, int qp, int n, const double* C, int ldc, 
 GQ_API int gq_set_guess(gq_batch* b, int qp, const double* y, const double* pi,
                  const double* lam, const double* t);
 
+/* ---- partial condensing (Sec. 3.5), host side ----
+ * Blocks of `block` consecutive stages of QP `qp` (stages kb..kb+block-1,
+ * the last block possibly shorter) become one stage: the states inside a
+ * block are eliminated through the dynamics, the new stage keeps the block's
+ * first state and stacks its controls; state bounds inside a block become
+ * general rows (after the stage's own general rows, stage by stage); the
+ * terminal stage is kept.  The condensed horizon is ceil(N / block).
+ * gq_condense_dims writes the condensed QP's dims (the format of
+ * gq_batch_memsize; dims may be NULL to query *len).  gq_condense fills
+ * QP dst_qp of `dst` (created with those dims and attached) through the
+ * setters.  gq_expand maps a condensed solution (y2, pi2, lam2, t2 in the
+ * layout of gq_get_sol_offsets for dst_qp) back to the original QP's (y,
+ * pi, lam, t): states by the block recursion, lambda and t by the
+ * constraint correspondence, the eliminated dynamics' multipliers from the
+ * eliminated states' stationarity rows.  Errors: GQ_ERR_ARG, GQ_ERR_DIMS,
+ * GQ_ERR_SIZE, and the setters' errors. */
+GQ_API int gq_condense_dims(const gq_batch* src, int qp, int block, int* dims, size_t cap, size_t* len);
+GQ_API int gq_condense(gq_batch* src, int src_qp, int block, gq_batch* dst, int dst_qp);
+GQ_API int gq_expand(gq_batch* src, int src_qp, int block, const gq_batch* dst, int dst_qp, const double* y2,
+                     const double* pi2, const double* lam2, const double* t2, double* y, double* pi, double* lam,
+                     double* t);
+
+/* Getters of the staged problem data, the inverse of the four setters above
+ * (same argument meaning and column-major layouts; any output may be NULL;
+ * the box getter returns idxbx relative to x).  Errors: GQ_ERR_ARG. */
+GQ_API int gq_get_dynamics(gq_batch* b, int qp, int n, double* A, int lda, double* B, int ldb, double* bvec);
+GQ_API int gq_get_cost(gq_batch* b, int qp, int n, double* Q, int ldq, double* S, int lds, double* R, int ldr,
+                       double* q, double* r);
+GQ_API int gq_get_box(gq_batch* b, int qp, int n, int* idxbu, double* lbu, double* ubu, int* idxbx, double* lbx,
+                      double* ubx);
+GQ_API int gq_get_general(gq_batch* b, int qp, int n, double* C, int ldc, double* D, int ldd, double* lg,
+                          double* ug);
+
 /* Initial state by elimination (Sec. 2.2 allows stage-wise sizes, so x_0 can
  * be removed: nx_0 = 0).  Stage 0 of QP `qp` must have nx_0 = 0; given the
  * measured state x0 (nx0 entries) and the stage-0 data that multiply it --

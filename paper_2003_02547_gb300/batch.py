@@ -84,13 +84,23 @@ class QpBatch:
     one shared data block.  Problem data are written with the C setters.
     """
 
-    def __init__(self, qps: Sequence, device: str = "cuda", share: bool = True, pinned: bool = True,
-                 set_data: bool = True):
+    def __init__(self, qps: Optional[Sequence], device: str = "cuda", share: bool = True, pinned: bool = True,
+                 set_data: bool = True, dims: Optional[Sequence[np.ndarray]] = None):
+        """``qps``: OcpQp objects; or None with ``dims``, one dims array per QP
+        (the C ABI format: N, then nx, nu, nbx, nbu, ng per stage), for a batch
+        whose data the caller writes through the C setters."""
         self.lib = gq.load()
-        self.qps = list(qps)
-        self.nqp = len(self.qps)
-        self.dims = dims_of(self.qps)
-        self.slots = slots_of(self.qps) if share else None
+        if qps is None:
+            self.qps = None
+            self.nqp = len(dims)
+            self.dims = np.ascontiguousarray(np.concatenate([np.asarray(d, dtype=np.int32) for d in dims]))
+            self.slots = None
+            set_data = False
+        else:
+            self.qps = list(qps)
+            self.nqp = len(self.qps)
+            self.dims = dims_of(self.qps)
+            self.slots = slots_of(self.qps) if share else None
         slot_p = _ptr(self.slots, ctypes.c_int) if self.slots is not None else None
         mem = self.lib.gq_batch_memsize(self.nqp, _ptr(self.dims, ctypes.c_int), self.dims.size, slot_p)
         if mem == 0:
@@ -160,6 +170,70 @@ class QpBatch:
                 self._sbase.append(acc)
                 acc += qp.N + 1
         return self._sbase[i]
+
+    def horizon(self, i: int) -> int:
+        pos = 0
+        for q in range(i):
+            pos += 1 + 5 * (int(self.dims[pos]) + 1)
+        return int(self.dims[pos])
+
+    def stage_dims(self, i: int):
+        """[(nx, nu, nbx, nbu, ng)] of QP i, from the dims array."""
+        pos = 0
+        for q in range(i):
+            pos += 1 + 5 * (int(self.dims[pos]) + 1)
+        N = int(self.dims[pos])
+        d = self.dims[pos + 1:pos + 1 + 5 * (N + 1)].reshape(N + 1, 5)
+        return [tuple(int(v) for v in row) for row in d]
+
+    def to_ocp(self, i: int):
+        """QP i as an OcpQp, read back from the staged data with the C getters
+        (for checking data written by C routines such as gq_condense)."""
+        from .workloads import OcpQp
+        L, h = self.lib, self.h
+        sd = self.stage_dims(i)
+        N = len(sd) - 1
+        nx = [d[0] for d in sd]
+        nu = [d[1] for d in sd]
+        f = lambda r, c: np.zeros((max(r, 1), max(c, 1)), order="F")
+        P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        PI = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        out = {k: [] for k in ("A", "B", "b", "Q", "S", "R", "q", "r", "idxbu", "lbu", "ubu", "idxbx", "lbx", "ubx",
+                               "C", "D", "lg", "ug")}
+        for n in range(N + 1):
+            x, u, nbx, nbu, ng = sd[n]
+            if n < N:
+                x1 = nx[n + 1]
+                A, B, bv = f(x1, x), f(x1, u), np.zeros(max(x1, 1))
+                gq.check(L.gq_get_dynamics(h, i, n, P(A), max(x1, 1), P(B), max(x1, 1), P(bv)))
+                out["A"].append(A[:x1, :x].copy())
+                out["B"].append(B[:x1, :u].copy())
+                out["b"].append(bv[:x1].copy())
+            Q, S, R, q, r = f(x, x), f(u, x), f(u, u), np.zeros(max(x, 1)), np.zeros(max(u, 1))
+            gq.check(L.gq_get_cost(h, i, n, P(Q), max(x, 1), P(S), max(u, 1), P(R), max(u, 1), P(q), P(r)))
+            out["Q"].append(Q[:x, :x].copy())
+            out["S"].append(S[:u, :x].copy())
+            out["R"].append(R[:u, :u].copy())
+            out["q"].append(q[:x].copy())
+            out["r"].append(r[:u].copy())
+            ibu, ibx = np.zeros(max(nbu, 1), dtype=np.int32), np.zeros(max(nbx, 1), dtype=np.int32)
+            lbu, ubu, lbx, ubx = (np.zeros(max(k, 1)) for k in (nbu, nbu, nbx, nbx))
+            gq.check(L.gq_get_box(h, i, n, PI(ibu), P(lbu), P(ubu), PI(ibx), P(lbx), P(ubx)))
+            out["idxbu"].append(ibu[:nbu].astype(np.int64))
+            out["lbu"].append(lbu[:nbu].copy())
+            out["ubu"].append(ubu[:nbu].copy())
+            out["idxbx"].append(ibx[:nbx].astype(np.int64))
+            out["lbx"].append(lbx[:nbx].copy())
+            out["ubx"].append(ubx[:nbx].copy())
+            C, D, lg, ug = f(ng, x), f(ng, u), np.zeros(max(ng, 1)), np.zeros(max(ng, 1))
+            gq.check(L.gq_get_general(h, i, n, P(C), max(ng, 1), P(D), max(ng, 1), P(lg), P(ug)))
+            out["C"].append(C[:ng, :x].copy())
+            out["D"].append(D[:ng, :u].copy())
+            out["lg"].append(lg[:ng].copy())
+            out["ug"].append(ug[:ng].copy())
+        qp = OcpQp(N=N, nx=nx, nu=nu, **out)
+        qp.validate()
+        return qp
 
     def set_all(self) -> None:
         done: set = set()

@@ -632,6 +632,87 @@ int gq_set_initial_state(gq_batch* b, int qp, const double* x0, int nx0, const d
   return GQ_OK;
 }
 
+// ---- getters of the staged problem data (inverse of the setters; any
+// output pointer may be NULL; column-major outputs with leading dimensions) ----
+int gq_get_dynamics(gq_batch* b, int qp, int n, double* A, int lda, double* B, int ldb, double* bvec) {
+  StageDesc* s;
+  int rc = stage_of(b, qp, n, &s);
+  if (rc) return rc;
+  if (n == b->qp[qp].N) return fail(GQ_ERR_ARG, "stage %d is terminal: no dynamics", n);
+  const int nx = s->nx, nu = s->nu, nx1 = s->nx1;
+  if ((A && nx && lda < nx1) || (B && nu && ldb < nx1)) return fail(GQ_ERR_ARG, "leading dimension too small");
+  const StageData lay = stage_data_layout(nx, nu, nx1, s->nbu + s->nbx, s->ng);
+  const double* D = host_data(b) + s->data;
+  for (int i = 0; i < nu && B; ++i)
+    for (int k = 0; k < nx1; ++k) B[k + (int64_t)i * ldb] = D[lay.BAt + (int64_t)i * lay.ldb + k];
+  for (int i = 0; i < nx && A; ++i)
+    for (int k = 0; k < nx1; ++k) A[k + (int64_t)i * lda] = D[lay.BAt + (int64_t)(nu + i) * lay.ldb + k];
+  for (int k = 0; k < nx1 && bvec; ++k) bvec[k] = D[lay.b + k];
+  return GQ_OK;
+}
+
+int gq_get_cost(gq_batch* b, int qp, int n, double* Q, int ldq, double* S, int lds, double* R, int ldr, double* q,
+                double* r) {
+  StageDesc* s;
+  int rc = stage_of(b, qp, n, &s);
+  if (rc) return rc;
+  const int nx = s->nx, nu = s->nu;
+  if ((Q && nx && ldq < nx) || (R && nu && ldr < nu) || (S && nu && nx && lds < nu))
+    return fail(GQ_ERR_ARG, "leading dimension too small");
+  const StageData lay = stage_data_layout(nx, nu, s->nx1, s->nbu + s->nbx, s->ng);
+  const double* D = host_data(b) + s->data;
+  const double* RSQ = D + lay.RSQ;
+  const int64_t lr = lay.ldr;
+  for (int i = 0; i < nu && R; ++i)
+    for (int j = 0; j < nu; ++j) R[i + (int64_t)j * ldr] = RSQ[i * lr + j];
+  for (int i = 0; i < nu && S; ++i)
+    for (int j = 0; j < nx; ++j) S[i + (int64_t)j * lds] = RSQ[i * lr + nu + j];
+  for (int i = 0; i < nx && Q; ++i)
+    for (int j = 0; j < nx; ++j) Q[i + (int64_t)j * ldq] = RSQ[(int64_t)(nu + i) * lr + nu + j];
+  for (int i = 0; i < nu && r; ++i) r[i] = D[lay.rq + i];
+  for (int i = 0; i < nx && q; ++i) q[i] = D[lay.rq + nu + i];
+  return GQ_OK;
+}
+
+int gq_get_box(gq_batch* b, int qp, int n, int* idxbu, double* lbu, double* ubu, int* idxbx, double* lbx,
+               double* ubx) {
+  StageDesc* s;
+  int rc = stage_of(b, qp, n, &s);
+  if (rc) return rc;
+  const int nbu = s->nbu, nbx = s->nbx, nb = nbu + nbx;
+  const StageData lay = stage_data_layout(s->nx, s->nu, s->nx1, nb, s->ng);
+  const double* D = host_data(b) + s->data;
+  const int32_t* I = reinterpret_cast<const int32_t*>(D + lay.box);
+  for (int k = 0; k < nbu; ++k) {
+    if (idxbu) idxbu[k] = I[k];
+    if (lbu) lbu[k] = D[lay.lo + k];
+    if (ubu) ubu[k] = D[lay.hi + k];
+  }
+  for (int k = 0; k < nbx; ++k) {
+    if (idxbx) idxbx[k] = I[nbu + k] - s->nu;
+    if (lbx) lbx[k] = D[lay.lo + nbu + k];
+    if (ubx) ubx[k] = D[lay.hi + nbu + k];
+  }
+  return GQ_OK;
+}
+
+int gq_get_general(gq_batch* b, int qp, int n, double* C, int ldc, double* Dm, int ldd, double* lg, double* ug) {
+  StageDesc* s;
+  int rc = stage_of(b, qp, n, &s);
+  if (rc) return rc;
+  const int ng = s->ng, nx = s->nx, nu = s->nu, nv = nx + nu, nb = s->nbu + s->nbx;
+  if ((C && nx && ng && ldc < ng) || (Dm && nu && ng && ldd < ng)) return fail(GQ_ERR_ARG, "leading dimension too small");
+  const StageData lay = stage_data_layout(nx, nu, s->nx1, nb, ng);
+  const double* D = host_data(b) + s->data;
+  for (int g = 0; g < ng; ++g) {
+    for (int i = 0; i < nu && Dm; ++i) Dm[g + (int64_t)i * ldd] = D[lay.DC + (int64_t)g * nv + i];
+    for (int i = 0; i < nx && C; ++i) C[g + (int64_t)i * ldc] = D[lay.DC + (int64_t)g * nv + nu + i];
+    if (lg) lg[g] = D[lay.lo + nb + g];
+    if (ug) ug[g] = D[lay.hi + nb + g];
+  }
+  return GQ_OK;
+}
+
 int gq_set_guess(gq_batch* b, int qp, const double* y, const double* pi, const double* lam,
                  const double* t) {
   int rc = check_batch(b);

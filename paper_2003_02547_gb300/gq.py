@@ -92,6 +92,15 @@ SIGNATURES = {
     "gq_set_box": (c_int, [c_void_p, c_int, c_int, P_int, P_double, P_double, P_int, P_double, P_double]),
     "gq_set_general": (c_int, [c_void_p, c_int, c_int, P_double, c_int, P_double, c_int, P_double, P_double]),
     "gq_set_guess": (c_int, [c_void_p, c_int, P_double, P_double, P_double, P_double]),
+    "gq_get_dynamics": (c_int, [c_void_p, c_int, c_int, P_double, c_int, P_double, c_int, P_double]),
+    "gq_get_cost": (c_int, [c_void_p, c_int, c_int, P_double, c_int, P_double, c_int, P_double, c_int,
+                            P_double, P_double]),
+    "gq_get_box": (c_int, [c_void_p, c_int, c_int, P_int, P_double, P_double, P_int, P_double, P_double]),
+    "gq_get_general": (c_int, [c_void_p, c_int, c_int, P_double, c_int, P_double, c_int, P_double, P_double]),
+    "gq_condense_dims": (c_int, [c_void_p, c_int, c_int, P_int, c_size_t, ctypes.POINTER(c_size_t)]),
+    "gq_condense": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
+    "gq_expand": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, P_double, P_double, P_double, P_double,
+                          P_double, P_double, P_double, P_double]),
     "gq_set_initial_state": (c_int, [c_void_p, c_int, P_double, c_int, P_double, c_int, P_double, P_double, c_int,
                                      P_double, P_double, c_int, P_double, P_double]),
     "gq_copy_qp": (c_int, [c_void_p, c_int, c_void_p, c_int]),
