@@ -531,7 +531,6 @@ def main():
     if rank == 0 and world == 1 and not a.no_extras:
         del singles
         extras["mass_spring_condensed_2_mixed"] = condensed_run(qps, 2, dev, gq.PREC_MIXED)
-        extras["mass_spring_condensed_3_mixed"] = condensed_run(qps, 3, dev, gq.PREC_MIXED)
         extras["single_small_qp_mixed"] = single_qp_latency(dev, gq.PREC_MIXED)
         extras["single_small_qp_fp64"] = single_qp_latency(dev, gq.PREC_FP64)
         extras["single_small_qp_mixed_graph"] = single_qp_latency(dev, gq.PREC_MIXED, graph=True)
