@@ -391,10 +391,10 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
   L.sol_bytes = o;
 
   o = 0;
-  int64_t* vecs[] = {&L.rg, &L.rb, &L.rd, &L.rm, &L.gt, &L.dy, &L.dpi, &L.dlam, &L.dt, &L.lp,
+  int64_t* vecs[] = {&L.rg, &L.rb, &L.rd, &L.rm, &L.dy, &L.dpi, &L.dlam, &L.dt, &L.lp,
                      &L.rg2, &L.rb2, &L.dy2, &L.dpi2, &L.dlam2, &L.dt2, &L.tinv};
-  const int64_t lens[] = {var, eq, side, side, var, var, eq, side, side, var, var, eq, var, eq, side, side, side};
-  for (int i = 0; i < 17; ++i) {
+  const int64_t lens[] = {var, eq, side, side, var, eq, side, side, var, var, eq, var, eq, side, side, side};
+  for (int i = 0; i < 16; ++i) {
     *vecs[i] = o;
     o = align_up(o + lens[i] * 8, 256);
   }
@@ -788,11 +788,11 @@ static int make_kernel_batch(gq_batch* b, Batch* k) {
   k->pi = reinterpret_cast<double*>(so + L.pi);
   k->lam = reinterpret_cast<double*>(so + L.lam);
   k->t = reinterpret_cast<double*>(so + L.t);
-  double** w[] = {&k->rg, &k->rb, &k->rd, &k->rm, &k->gt, &k->dy, &k->dpi, &k->dlam, &k->dt, &k->lp,
+  double** w[] = {&k->rg, &k->rb, &k->rd, &k->rm, &k->dy, &k->dpi, &k->dlam, &k->dt, &k->lp,
                   &k->rg2, &k->rb2, &k->dy2, &k->dpi2, &k->dlam2, &k->dt2, &k->tinv};
-  const int64_t off[] = {L.rg, L.rb, L.rd, L.rm, L.gt, L.dy, L.dpi, L.dlam, L.dt, L.lp,
+  const int64_t off[] = {L.rg, L.rb, L.rd, L.rm, L.dy, L.dpi, L.dlam, L.dt, L.lp,
                          L.rg2, L.rb2, L.dy2, L.dpi2, L.dlam2, L.dt2, L.tinv};
-  for (int i = 0; i < 17; ++i) *w[i] = reinterpret_cast<double*>(ws + off[i]);
+  for (int i = 0; i < 16; ++i) *w[i] = reinterpret_cast<double*>(ws + off[i]);
   k->fac = ws + L.fac;
   k->matg = reinterpret_cast<double*>(ws + L.matg);
   if (b->nwarp < b->nqp) {

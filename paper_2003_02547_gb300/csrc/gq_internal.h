@@ -83,7 +83,7 @@ struct Layout {
   // "sol" buffer
   int64_t stats, y, pi, lam, t, sol_bytes;
   // workspace: FP64 vectors then the factor arena
-  int64_t rg, rb, rd, rm, gt, dy, dpi, dlam, dt, lp, rg2, rb2, dy2, dpi2, dlam2, dt2, tinv, fac, data32, matg, ws_bytes;
+  int64_t rg, rb, rd, rm, dy, dpi, dlam, dt, lp, rg2, rb2, dy2, dpi2, dlam2, dt2, tinv, fac, data32, matg, ws_bytes;
 };
 
 // Kernel launch parameters (passed by value).
@@ -98,7 +98,7 @@ struct Batch {
   float* data32;          // FP32 mirror of `data` (same element layout)
   gq_stats* stats;
   double *y, *pi, *lam, *t;
-  double *rg, *rb, *rd, *rm, *gt, *dy, *dpi, *dlam, *dt, *lp, *rg2, *rb2, *dy2, *dpi2, *dlam2, *dt2, *tinv;
+  double *rg, *rb, *rd, *rm, *dy, *dpi, *dlam, *dt, *lp, *rg2, *rb2, *dy2, *dpi2, *dlam2, *dt2, *tinv;
   void* fac;
   double* matg;           // per-QP stage-matrix scratch of the block kernel (global mode only)
 };

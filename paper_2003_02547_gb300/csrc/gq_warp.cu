@@ -1121,11 +1121,11 @@ template <typename T>
 static cudaError_t launch_one(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
                               LaunchKind kind, double sigma_mu, const DirOut& o, const int32_t* order, int count) {
   const WarpPlan P = warp_plan(b, sh, (int)sizeof(T));
-  static size_t attr_bytes = 48 * 1024;
-  if (P.bytes > attr_bytes) {
+  // opt in to more than the default dynamic shared memory on the current
+  // device (no cache shared between host threads or devices)
+  if (P.bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(warp_ipm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.bytes);
     if (e != cudaSuccess) return e;
-    attr_bytes = P.bytes;
   }
   warp_ipm_kernel<T><<<count, 32, P.bytes, stream>>>(b, P, arg, (int)kind, sigma_mu, o, order);
   return cudaGetLastError();
