@@ -87,6 +87,10 @@ extern "C" {
 /* ---- solver arguments (Sec. 4.2) ---- */
 #define GQ_MODE_SPEED 0     /* delta formulation, residual-based exit (Sec. 4.2) */
 #define GQ_MODE_BALANCE 1   /* speed + iterative refinement of every direction   */
+#define GQ_MODE_ROBUST 2    /* balance + every Riccati factorisation by the array
+                               algorithm: chol(Ht + M M') taken from the QR
+                               factorisation of [chol(Ht)'; M'] without forming
+                               M M' (Sec. 4.2, mode robust); block kernel only */
 #define GQ_PREC_FP64 0      /* Riccati factor/solve in FP64                       */
 #define GQ_PREC_MIXED 1     /* Riccati factor/solve in FP32, residuals, IR,
                                step length and duality measure in FP64          */

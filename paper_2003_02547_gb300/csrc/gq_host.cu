@@ -153,7 +153,8 @@ const char* gq_last_error(void) { return g_err; }
 
 int gq_ipm_arg_default(gq_ipm_arg* arg, int mode, int precision) {
   if (arg == nullptr) return fail(GQ_ERR_ARG, "arg is NULL");
-  if (mode != GQ_MODE_SPEED && mode != GQ_MODE_BALANCE) return fail(GQ_ERR_ARG, "unknown mode %d", mode);
+  if (mode != GQ_MODE_SPEED && mode != GQ_MODE_BALANCE && mode != GQ_MODE_ROBUST)
+    return fail(GQ_ERR_ARG, "unknown mode %d", mode);
   if (precision != GQ_PREC_FP64 && precision != GQ_PREC_MIXED)
     return fail(GQ_ERR_ARG, "unknown precision %d", precision);
   std::memset(arg, 0, sizeof(*arg));
@@ -170,7 +171,7 @@ int gq_ipm_arg_default(gq_ipm_arg* arg, int mode, int precision) {
   arg->tau_b = 0.995;
   arg->corr_k = 2.0;
   arg->reg_prim = mixed ? 1e-9 : 0.0;
-  arg->ir_steps = (mixed || mode == GQ_MODE_BALANCE) ? 3 : 0;
+  arg->ir_steps = (mixed || mode != GQ_MODE_SPEED) ? 3 : 0;
   // refine to 1e-12 relative: a looser inexact-Newton tolerance (1e-4) was
   // measured to skip refinement but raise the mass-spring iteration count
   // from 7.0 to 10.6, a net loss
@@ -758,11 +759,13 @@ int gq_download(gq_batch* b, void* stream) {
 
 // the classical Riccati variant is implemented in the block kernel only
 static int check_variant(const gq_batch* b, const gq_ipm_arg* a) {
-  if (a->riccati == 1 && b->nwarp > 0)
+  if ((a->riccati == 1 || a->mode == GQ_MODE_ROBUST) && b->nwarp > 0)
     return fail(GQ_ERR_ARG,
-                "classical Riccati runs in the block kernel: set the schedule's warp_max_nv to 0 "
-                "(%d QPs are in the warp bucket)",
+                "the classical Riccati variant and the robust mode run in the block kernel: set the "
+                "schedule's warp_max_nv to 0 (%d QPs are in the warp bucket)",
                 b->nwarp);
+  if (a->riccati == 1 && a->mode == GQ_MODE_ROBUST)
+    return fail(GQ_ERR_ARG, "the robust mode's array algorithm is the square-root Riccati variant");
   return GQ_OK;
 }
 
@@ -821,7 +824,8 @@ static cudaError_t launch_all(gq_batch* b, const Batch& k, const gq_ipm_arg& arg
 
 static int check_arg(const gq_ipm_arg* a) {
   if (a == nullptr) return fail(GQ_ERR_ARG, "arg is NULL");
-  if (a->mode != GQ_MODE_SPEED && a->mode != GQ_MODE_BALANCE) return fail(GQ_ERR_ARG, "unknown mode");
+  if (a->mode != GQ_MODE_SPEED && a->mode != GQ_MODE_BALANCE && a->mode != GQ_MODE_ROBUST)
+    return fail(GQ_ERR_ARG, "unknown mode");
   if (a->precision != GQ_PREC_FP64 && a->precision != GQ_PREC_MIXED) return fail(GQ_ERR_ARG, "unknown precision");
   if (a->iter_max < 0 || a->ir_steps < 0 || a->ir_steps > 64) return fail(GQ_ERR_ARG, "iter_max/ir_steps out of range");
   if (a->warm_start < 0 || a->warm_start > 2) return fail(GQ_ERR_ARG, "warm_start must be 0, 1 or 2");

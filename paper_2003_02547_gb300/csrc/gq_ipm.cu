@@ -138,6 +138,7 @@ struct Ctx {
   void* mat;  // matrix scratch (Tf): L_{n+1}, Phi, M
   int nvmax, nxmax;
   bool classical;  // classical Riccati: explicit P_{n+1} in place of L_{n+1}
+  bool array_qr;   // robust mode: chol(Ht + M M') by QR of [chol(Ht)'; M']
   Ring ring;
 };
 
@@ -479,7 +480,7 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
     // Phi = RSQ + M M' + [D C]' W [D C] + diagonal terms, lower strips
     {
       const int nNT = (nv + 7) / 8, nNG = (nNT + 3) / 4;
-      const int kend = n < C.N ? nx1 : 0;
+      const int kend = (n < C.N && !C.array_qr) ? nx1 : 0;
       for (int u = w; u < nMT * nNG; u += NW) {
         const int mt = u / nNG, nt0 = (u - mt * nNG) * 4;
         if (nt0 * 8 > mt * 16 + 15) continue;  // strip above the diagonal
@@ -595,7 +596,7 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
   #pragma unroll
           for (int c = 0; c < kT; ++c) acc[r][c] += a[r] * bb[c];
       }
-      if (n < C.N) {
+      if (n < C.N && !C.array_qr) {
         for (int k = 0; k < nx1; ++k) {
           const Tf* mk = sMt + k * ldP;
           Tf a[kT], bb[kT];
@@ -713,6 +714,37 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
     __syncthreads();
   }
   ok = __syncthreads_and(ok) != 0;
+  if (C.array_qr && n < C.N && nx1 > 0) {
+    // robust mode: Phi = Lh Lh' + M M' without forming M M'.  The factor of
+    // Phi is the transposed triangle of the QR factorisation of the array
+    // [Lh'; M']; column j's Householder reflector acts on row j of Lh' (the
+    // stored column j of Lh) and on column j of M' (nx1 entries), and is
+    // applied to the columns c > j of both.
+    for (int j = 0; j < nv; ++j) {
+      Tf* mj = sMt;  // M'[k][j] = sMt[k * ldP + j]
+      const Tf alpha = sPhi[j * ldP + j];
+      double ss = 0.0;
+      for (int k = 0; k < nx1; ++k) ss += (double)mj[k * ldP + j] * (double)mj[k * ldP + j];
+      const Tf sigma = (Tf)sqrt((double)alpha * (double)alpha + ss);
+      // reflector u = [alpha - sigma; M'[:, j]] (alpha > 0, sigma >= alpha:
+      // u0 <= 0 with no cancellation when ss is small relative to alpha^2
+      // handled by the equivalent form u0 = -ss / (alpha + sigma))
+      const Tf u0 = (Tf)(-ss / ((double)alpha + (double)sigma));
+      const double utu = (double)u0 * (double)u0 + ss;
+      const Tf beta = utu > 0.0 ? (Tf)(2.0 / utu) : (Tf)0;
+      for (int c = j + 1 + tid; c < nv; c += NT) {
+        // column c: top entry R[j][c] = Lh-stored (c, j); then M'[:, c]
+        Tf wv = u0 * sPhi[c * ldP + j];
+        for (int k = 0; k < nx1; ++k) wv += mj[k * ldP + j] * sMt[k * ldP + c];
+        const Tf bw = beta * wv;
+        sPhi[c * ldP + j] -= bw * u0;
+        for (int k = 0; k < nx1; ++k) sMt[k * ldP + c] -= bw * mj[k * ldP + j];
+      }
+      __syncthreads();
+      if (tid == 0) sPhi[j * ldP + j] = sigma;
+      __syncthreads();
+    }
+  }
   // X = L_ee^{-1} (lower), column j by thread j, into the M' buffer (ld ne)
   for (int j = tid; j < ne; j += NT) {
     sMt[j * ne + j] = (Tf)1 / sPhi[j * ldP + j];
@@ -1062,6 +1094,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
   C.ring.fac_off = (uint32_t)P.ring_fac;
   C.ring.staged = P.staged;
   C.classical = arg.riccati == 1;
+  C.array_qr = arg.mode == GQ_MODE_ROBUST;
   C.ring.ok = true;
 
   // count active sides (integer count: exact in any order)
@@ -1246,7 +1279,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
       newton_dir<double>(C, d, 0, 0.0, &cnt);
     else
       newton_dir<float>(C, d, 0, 0.0, &cnt);
-    const int ir = (mixed && !fp64) || arg.mode == GQ_MODE_BALANCE ? arg.ir_steps : 0;
+    const int ir = (mixed && !fp64) || arg.mode != GQ_MODE_SPEED ? arg.ir_steps : 0;
     // a refined FP32 direction must also be an inexact-Newton step for the
     // unscaled exit rule: its own residual well below the iterate's
     const double inexact = kInexact * fmax(fmax(r.g, r.b), arg.tol_stat);

@@ -16,7 +16,7 @@ GQ_ERR_ARG, GQ_ERR_DIMS, GQ_ERR_SIZE, GQ_ERR_CUDA, GQ_ERR_DATA, GQ_ERR_STATE = -
 STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_MIN_STEP, STATUS_NAN, STATUS_TIMEOUT = 0, 1, 2, 3, 4
 FLAG_FP64_FALLBACK = 1
 FLAG_REGULARIZED = 2
-MODE_SPEED, MODE_BALANCE = 0, 1
+MODE_SPEED, MODE_BALANCE, MODE_ROBUST = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 

@@ -117,9 +117,11 @@ def test_residual_norms_match_oracle(env):
 # ----------------------------------------------------------------------------
 # a2-a4: one Newton direction through the Riccati factorisation
 # ----------------------------------------------------------------------------
-def _newton_compare(env, qps, precision, ir_steps, tol, sigma_mu=0.37, ir_tol=None):
+def _newton_compare(env, qps, precision, ir_steps, tol, sigma_mu=0.37, ir_tol=None, mode=0):
     gq, QpBatch, torch = env
     b = QpBatch(qps)
+    if mode == 2:
+        b.set_schedule(0, 256)        # the robust mode runs in the block kernel
     its = []
     for i, qp in enumerate(qps):
         dq = O.assemble(qp)
@@ -129,7 +131,7 @@ def _newton_compare(env, qps, precision, ir_steps, tol, sigma_mu=0.37, ir_tol=No
     b.upload()
     b.upload_sol()
     out = torch.zeros_like(b.dev_sol)
-    arg = gq.default_arg(0, precision, ir_steps=ir_steps)
+    arg = gq.default_arg(mode, precision, ir_steps=ir_steps)
     if ir_tol is not None:
         arg.ir_tol = ir_tol
     b.newton_step(arg, sigma_mu, out)
@@ -420,3 +422,21 @@ def test_classical_riccati_matches_square_root_on_convex_qps(env):
     with pytest.raises(gq.GqError) as e:
         b.solve(gq.default_arg(0, 0, riccati=1))
     assert e.value.code == gq.GQ_ERR_ARG
+
+
+def test_robust_mode_array_algorithm_matches_oracle(env):
+    """Mode robust (Sec. 4.2): every Riccati factor from the QR array
+    algorithm; one Newton direction at random iterates equals the oracle's
+    (FP64, 1e-9), and full solves meet the oracle gates in both precisions."""
+    gq, QpBatch, torch = env
+    qps = [W.small_random_qp(2), W.mass_spring_qp(4)] + mixed_set()[:2] + [W.ragged_random_qp(1)]
+    _newton_compare(env, qps, precision=0, ir_steps=0, tol=1e-9, mode=2)
+    refs = [oracle_pair(q) for q in qps]
+    for prec in (0, 1):
+        b = QpBatch(qps)
+        b.set_schedule(0, 256)
+        b.upload()
+        b.solve(gq.default_arg(2, prec))
+        b.download()
+        torch.cuda.synchronize()
+        _check_converged(b, qps, refs)
