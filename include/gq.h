@@ -83,14 +83,20 @@ extern "C" {
                                     and, if still indefinite, the iteration
                                     was redone with lambda, t lifted to
                                     max(1e-10, 1e-2 max(|r_g|, |r_b|))       */
+#define GQ_FLAG_ARRAY_QR 4       /* mode balance: refinement fell short of the accuracy
+                                    rule, so the rest of the solve factors with the QR
+                                    array algorithm */
 
 /* ---- solver arguments (Sec. 4.2) ---- */
 #define GQ_MODE_SPEED 0     /* delta formulation, residual-based exit (Sec. 4.2) */
-#define GQ_MODE_BALANCE 1   /* speed + iterative refinement of every direction   */
+#define GQ_MODE_BALANCE 1   /* speed + iterative refinement of every direction;
+                               a direction that refinement cannot make accurate
+                               (ir_fail_ratio) switches the QP's factorisations
+                               to the array algorithm below (Sec. 4.2)          */
 #define GQ_MODE_ROBUST 2    /* balance + every Riccati factorisation by the array
                                algorithm: chol(Ht + M M') taken from the QR
                                factorisation of [chol(Ht)'; M'] without forming
-                               M M' (Sec. 4.2, mode robust); block kernel only */
+                               M M' (Sec. 4.2, mode robust)                     */
 #define GQ_PREC_FP64 0      /* Riccati factor/solve in FP64                       */
 #define GQ_PREC_MIXED 1     /* Riccati factor/solve in FP32, residuals, IR,
                                step length and duality measure in FP64          */
@@ -123,12 +129,18 @@ typedef struct gq_ipm_arg {
     double ir_tol;         /* IR stops when ||res||inf <= ir_tol ||rhs||inf          */
     double warm_min;       /* warm start 2: lambda, t clamped below by this         */
     int64_t timeout_ns;    /* per-QP device wall-clock limit, 0 = none             */
+    double ir_fail_ratio;  /* a refined direction whose residual ratio exceeds this
+                              (or whose residual is not an inexact-Newton step)
+                              counts as inaccurate: the mixed path then refactors
+                              in FP64 (fp64_fallback), and mode balance then
+                              refactors with the QR array algorithm (Sec. 4.2) */
 } gq_ipm_arg;
 
 /* Defaults for a mode and precision: iter_max 100, tolerances 1e-8,
  * alpha_min 1e-12, lam_min = t_min = 1e-16 (FP64) or 1e-12 (mixed),
  * tau_b 0.995, corr_k 2, reg_prim 0 (FP64) or 1e-9 (mixed), ir_steps 0
- * (FP64 speed) or 3 (mixed or balance), ir_tol 1e-12, warm_min 1e-2.
+ * (FP64 speed) or 3 (mixed, balance or robust), ir_tol 1e-12, warm_min 1e-2,
+ * ir_fail_ratio 1e-6.
  * Returns GQ_ERR_ARG on a null pointer or unknown mode/precision. */
 GQ_API int gq_ipm_arg_default(gq_ipm_arg* arg, int mode, int precision);
 

@@ -178,6 +178,7 @@ int gq_ipm_arg_default(gq_ipm_arg* arg, int mode, int precision) {
   arg->ir_tol = 1e-12;
   arg->warm_min = 1e-2;
   arg->timeout_ns = 0;
+  arg->ir_fail_ratio = 1e-6;
   return GQ_OK;
 }
 
@@ -759,10 +760,10 @@ int gq_download(gq_batch* b, void* stream) {
 
 // the classical Riccati variant is implemented in the block kernel only
 static int check_variant(const gq_batch* b, const gq_ipm_arg* a) {
-  if ((a->riccati == 1 || a->mode == GQ_MODE_ROBUST) && b->nwarp > 0)
+  if (a->riccati == 1 && b->nwarp > 0)
     return fail(GQ_ERR_ARG,
-                "the classical Riccati variant and the robust mode run in the block kernel: set the "
-                "schedule's warp_max_nv to 0 (%d QPs are in the warp bucket)",
+                "classical Riccati runs in the block kernel: set the schedule's warp_max_nv to 0 "
+                "(%d QPs are in the warp bucket)",
                 b->nwarp);
   if (a->riccati == 1 && a->mode == GQ_MODE_ROBUST)
     return fail(GQ_ERR_ARG, "the robust mode's array algorithm is the square-root Riccati variant");
@@ -834,6 +835,7 @@ static int check_arg(const gq_ipm_arg* a) {
   if (!(a->lam_min > 0.0 && a->t_min > 0.0)) return fail(GQ_ERR_ARG, "lam_min and t_min must be positive");
   if (!(a->reg_prim >= 0.0)) return fail(GQ_ERR_ARG, "reg_prim must be >= 0");
   if (a->timeout_ns < 0) return fail(GQ_ERR_ARG, "timeout_ns must be >= 0");
+  if (!(a->ir_fail_ratio >= 0.0)) return fail(GQ_ERR_ARG, "ir_fail_ratio must be >= 0");
   return GQ_OK;
 }
 

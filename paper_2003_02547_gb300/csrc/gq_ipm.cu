@@ -79,7 +79,6 @@ __host__ __device__ SmemPlan smem_plan(const Batch& b, const Shape& sh) {
 
 namespace {
 
-constexpr double kIrFailRatio = 1e-6;      // mixed path: refinement residual ratio that triggers FP64 factors
 constexpr double kLift = 1e-10;          // smallest floor of lambda, t after a lost FP64 pivot
 constexpr double kLiftRel = 1e-2;        // ... relative to the stationarity residual
 constexpr double kRegRetry = 1e-10;        // primal regularisation of an FP64 refactorisation after a lost pivot
@@ -1305,11 +1304,20 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
                        : newton_dir<float>(C, d, ir, arg.ir_tol, &cnt);
         }
       }
-      if (!fp64 && arg.fp64_fallback && ir > 0 && !(ratio <= kIrFailRatio && cnt.m <= inexact)) {
-        // a7 failed to recover the accuracy of the FP32 factors: refactor in FP64
-        fp64 = true;
-        flags |= GQ_FLAG_FP64_FALLBACK;
-        continue;
+      if (ir > 0 && !(ratio <= arg.ir_fail_ratio && cnt.m <= inexact)) {
+        // a7 failed to make the direction accurate: refactor in FP64 (mixed
+        // path), else, in mode balance, with the array algorithm (Sec. 4.2),
+        // and redo this iteration
+        if (!fp64 && arg.fp64_fallback) {
+          fp64 = true;
+          flags |= GQ_FLAG_FP64_FALLBACK;
+          continue;
+        }
+        if (arg.mode == GQ_MODE_BALANCE && !C.array_qr && !C.classical) {
+          C.array_qr = true;
+          flags |= GQ_FLAG_ARRAY_QR;
+          continue;
+        }
       }
       alpha = fmin(1.0, arg.tau_b * max_step(C, d.dlam, d.dt));
     } else {
@@ -1317,10 +1325,17 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
         // no inequalities: refine the single Newton step
         const double ratio = fp64 ? newton_dir<double>(C, d, ir, arg.ir_tol, &cnt)
                                   : newton_dir<float>(C, d, ir, arg.ir_tol, &cnt);
-        if (!fp64 && arg.fp64_fallback && !(ratio <= kIrFailRatio && cnt.m <= inexact)) {
-          fp64 = true;
-          flags |= GQ_FLAG_FP64_FALLBACK;
-          continue;
+        if (!(ratio <= arg.ir_fail_ratio && cnt.m <= inexact)) {
+          if (!fp64 && arg.fp64_fallback) {
+            fp64 = true;
+            flags |= GQ_FLAG_FP64_FALLBACK;
+            continue;
+          }
+          if (arg.mode == GQ_MODE_BALANCE && !C.array_qr && !C.classical) {
+            C.array_qr = true;
+            flags |= GQ_FLAG_ARRAY_QR;
+            continue;
+          }
         }
       }
       alpha = 1.0;

@@ -31,7 +31,6 @@ namespace {
 using namespace dev;
 
 constexpr int LDS = 33;                 // shared-memory row stride
-constexpr double kIrFailRatio = 1e-6;   // mixed path: refinement residual ratio that hands the QP to FP64
 constexpr double kLift = 1e-10;          // smallest floor of lambda, t after a lost FP64 pivot
 constexpr double kLiftRel = 1e-2;        // ... relative to the stationarity residual
 constexpr double kRegRetry = 1e-10;     // primal regularisation of an FP64 refactorisation after a lost pivot
@@ -67,6 +66,7 @@ struct WCtx {
   void* sP;    // Phi and its factor, 32 x LDS
   double* sv;  // per-constraint scratch (vmax doubles)
   int vmax;
+  bool qr;     // array algorithm: chol(Ht + M M') by QR of [chol(Ht)'; M']
 };
 
 // deterministic sum over this QP's sides: 32-side chunks by butterfly, chunk
@@ -350,7 +350,7 @@ __device__ __forceinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double
     const float* swf = reinterpret_cast<const float*>(sw);
     float* pf = reinterpret_cast<float*>(sP);
     const int ldr = L.ldr, ng = s.ng;
-    const bool prod = n < C.N;
+    const bool prod = n < C.N && !C.qr;
     const int g = lane >> 2, q = lane & 3;
     for (int mt = 0; mt * 16 < nv; ++mt) {
       for (int nt = 0; nt * 8 < nv && nt * 8 <= mt * 16 + 15; ++nt) {
@@ -397,7 +397,7 @@ __device__ __forceinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double
   } else if (act) {
     const T* rs = D + L.RSQ + (int64_t)i * L.ldr;
     const T* mi = sM + i * LDS;
-    const bool prod = n < C.N;
+    const bool prod = n < C.N && !C.qr;
     for (int j = 0; j <= i; ++j) {
       const T* mj = sM + j * LDS;
       T a0 = rs[j], a1 = T(0), a2 = T(0), a3 = T(0);
@@ -448,6 +448,34 @@ __device__ __forceinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double
     const T r = good ? wrsqrt<T>(d) : T(1);
     if (act && i >= k) sP[i * LDS + k] = sk * r;  // i == k: d / sqrt(d)
     __syncwarp();
+  }
+  if (C.qr && n < C.N) {
+    // array algorithm (Sec. 4.2): sP holds Lh = chol(Ht) and sM the rows of
+    // M; the factor of Ht + M M' is the transposed R of the QR factorisation
+    // of [Lh'; M'].  Reflector j zeroes column j of M' (row j of sM) against
+    // the pivot Lh[j][j] and acts on row j of Lh' and on M' only; lane c > j
+    // applies it to its own column (row c of Lh and of sM).
+    for (int j = 0; j < nv; ++j) {
+      const T* mj = sM + j * LDS;
+      const T alpha = sP[j * LDS + j];
+      T ss = T(0);
+      for (int k = 0; k < nx1; ++k) ss += mj[k] * mj[k];
+      const T sigma = sqrt(alpha * alpha + ss);
+      const T u0 = -ss / (alpha + sigma);  // alpha - sigma without cancellation
+      const T utu = u0 * u0 + ss;
+      const T beta = utu > T(0) ? T(2) / utu : T(0);
+      __syncwarp();
+      if (act && i > j) {
+        T* mi = sM + i * LDS;
+        T wv = u0 * sP[i * LDS + j];
+        for (int k = 0; k < nx1; ++k) wv += mj[k] * mi[k];
+        const T bw = beta * wv;
+        sP[i * LDS + j] -= bw * u0;
+        for (int k = 0; k < nx1; ++k) mi[k] -= bw * mj[k];
+      }
+      if (lane == j) sP[j * LDS + j] = sigma;
+      __syncwarp();
+    }
   }
   // X = L_ee^{-1}: lane j computes column j (entries i >= j) into sM
   if (lane < ne) {
@@ -801,6 +829,7 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
   C.sP = smem + P.sP;
   C.sv = reinterpret_cast<double*>(smem + P.sv);
   C.vmax = P.vmax;
+  C.qr = arg.mode == GQ_MODE_ROBUST;
 
   // active sides (integer count, exact)
   {
@@ -1001,7 +1030,7 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
       break;
     }
     wnewton<T>(C, d, 0, 0.0, &cnt);
-    const int ir = (mixed && !fp64) || arg.mode == GQ_MODE_BALANCE ? arg.ir_steps : 0;
+    const int ir = (mixed && !fp64) || arg.mode != GQ_MODE_SPEED ? arg.ir_steps : 0;
     // a refined FP32 direction must also be an inexact-Newton step for the
     // unscaled exit rule: its own residual well below the iterate's
     const double inexact = kInexact * fmax(fmax(r.g, r.b), arg.tol_stat);
@@ -1024,19 +1053,34 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
           ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
         }
       }
-      if (!fp64 && arg.fp64_fallback && ir > 0 && !(ratio <= kIrFailRatio && cnt.m <= inexact)) {
-        // refinement could not recover the FP32 factors' accuracy: the FP64
-        // launch continues this QP from the current iterate
-        status = kStatusResumeFp64;
-        break;
+      if (ir > 0 && !(ratio <= arg.ir_fail_ratio && cnt.m <= inexact)) {
+        // refinement could not make the direction accurate: the FP64 launch
+        // continues this QP from the current iterate (mixed path), else, in
+        // mode balance, this iteration is redone with the array algorithm
+        if (!fp64 && arg.fp64_fallback) {
+          status = kStatusResumeFp64;
+          break;
+        }
+        if (arg.mode == GQ_MODE_BALANCE && !C.qr) {
+          C.qr = true;
+          flags |= GQ_FLAG_ARRAY_QR;
+          continue;
+        }
       }
       alpha = fmin(1.0, arg.tau_b * wmax_step(C, d.dlam, d.dt));
     } else {
       if (ir > 0) {
         const double ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
-        if (!fp64 && arg.fp64_fallback && !(ratio <= kIrFailRatio && cnt.m <= inexact)) {
-          status = kStatusResumeFp64;
-          break;
+        if (!(ratio <= arg.ir_fail_ratio && cnt.m <= inexact)) {
+          if (!fp64 && arg.fp64_fallback) {
+            status = kStatusResumeFp64;
+            break;
+          }
+          if (arg.mode == GQ_MODE_BALANCE && !C.qr) {
+            C.qr = true;
+            flags |= GQ_FLAG_ARRAY_QR;
+            continue;
+          }
         }
       }
       alpha = 1.0;

@@ -16,6 +16,7 @@ GQ_ERR_ARG, GQ_ERR_DIMS, GQ_ERR_SIZE, GQ_ERR_CUDA, GQ_ERR_DATA, GQ_ERR_STATE = -
 STATUS_CONVERGED, STATUS_MAX_ITER, STATUS_MIN_STEP, STATUS_NAN, STATUS_TIMEOUT = 0, 1, 2, 3, 4
 FLAG_FP64_FALLBACK = 1
 FLAG_REGULARIZED = 2
+FLAG_ARRAY_QR = 4
 MODE_SPEED, MODE_BALANCE, MODE_ROBUST = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
@@ -33,7 +34,7 @@ class IpmArg(ctypes.Structure):
                 ("tol_stat", c_double), ("tol_eq", c_double), ("tol_ineq", c_double), ("tol_comp", c_double),
                 ("alpha_min", c_double), ("lam_min", c_double), ("t_min", c_double), ("tau_b", c_double),
                 ("corr_k", c_double), ("reg_prim", c_double), ("ir_tol", c_double), ("warm_min", c_double),
-                ("timeout_ns", c_int64)]
+                ("timeout_ns", c_int64), ("ir_fail_ratio", c_double)]
 
 
 class Stats(ctypes.Structure):

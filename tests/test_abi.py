@@ -47,7 +47,7 @@ def test_binding_names_match_header(gqmod):
 
 
 def test_struct_sizes_match_header(gqmod):
-    assert ctypes.sizeof(gqmod.IpmArg) == 8 * 4 + 12 * 8 + 8
+    assert ctypes.sizeof(gqmod.IpmArg) == 8 * 4 + 12 * 8 + 8 + 8
     assert ctypes.sizeof(gqmod.Stats) == 64
     assert ctypes.sizeof(gqmod.ServerCfg) == 4 * 4 + 8 + ctypes.sizeof(gqmod.IpmArg) + 8
     assert ctypes.sizeof(gqmod.Request) == 8 + 4 + 4 + 8 + 8 + 4 * 8

@@ -117,11 +117,11 @@ def test_residual_norms_match_oracle(env):
 # ----------------------------------------------------------------------------
 # a2-a4: one Newton direction through the Riccati factorisation
 # ----------------------------------------------------------------------------
-def _newton_compare(env, qps, precision, ir_steps, tol, sigma_mu=0.37, ir_tol=None, mode=0):
+def _newton_compare(env, qps, precision, ir_steps, tol, sigma_mu=0.37, ir_tol=None, mode=0, schedule=None):
     gq, QpBatch, torch = env
     b = QpBatch(qps)
-    if mode == 2:
-        b.set_schedule(0, 256)        # the robust mode runs in the block kernel
+    if schedule is not None:
+        b.set_schedule(*schedule)
     its = []
     for i, qp in enumerate(qps):
         dq = O.assemble(qp)
@@ -424,19 +424,48 @@ def test_classical_riccati_matches_square_root_on_convex_qps(env):
     assert e.value.code == gq.GQ_ERR_ARG
 
 
-def test_robust_mode_array_algorithm_matches_oracle(env):
+@pytest.mark.parametrize("warp_max_nv", [32, 0])
+def test_robust_mode_array_algorithm_matches_oracle(env, warp_max_nv):
     """Mode robust (Sec. 4.2): every Riccati factor from the QR array
-    algorithm; one Newton direction at random iterates equals the oracle's
-    (FP64, 1e-9), and full solves meet the oracle gates in both precisions."""
+    algorithm, in the one-warp kernel (QPs with nv <= 32) and in the block
+    kernel (warp_max_nv = 0: all QPs).  One Newton direction at random
+    iterates equals the oracle's (FP64, 1e-9), and full solves meet the
+    oracle gates in both precisions."""
     gq, QpBatch, torch = env
     qps = [W.small_random_qp(2), W.mass_spring_qp(4)] + mixed_set()[:2] + [W.ragged_random_qp(1)]
-    _newton_compare(env, qps, precision=0, ir_steps=0, tol=1e-9, mode=2)
+    _newton_compare(env, qps, precision=0, ir_steps=0, tol=1e-9, mode=2, schedule=(warp_max_nv, 256))
     refs = [oracle_pair(q) for q in qps]
     for prec in (0, 1):
         b = QpBatch(qps)
-        b.set_schedule(0, 256)
+        b.set_schedule(warp_max_nv, 256)
         b.upload()
         b.solve(gq.default_arg(2, prec))
         b.download()
         torch.cuda.synchronize()
+        _check_converged(b, qps, refs)
+
+
+@pytest.mark.parametrize("warp_max_nv", [32, 0])
+def test_balance_mode_switches_to_array_algorithm(env, warp_max_nv):
+    """Mode balance (Sec. 4.2): a direction that refinement cannot make
+    accurate repeats the factorisation with the array algorithm.  With
+    ir_fail_ratio = 0 every refined direction counts as inaccurate, so every
+    QP takes the whole chain (mixed: FP32 -> FP64 factors -> array
+    algorithm; FP64: Cholesky -> array algorithm) and must still meet the
+    oracle gates."""
+    gq, QpBatch, torch = env
+    qps = [W.small_random_qp(i) for i in range(2)] + [W.mass_spring_qp(3)] + mixed_set()[:2] \
+        + [W.ragged_random_qp(1)]
+    refs = [oracle_pair(q) for q in qps]
+    for prec in (0, 1):
+        b = QpBatch(qps)
+        b.set_schedule(warp_max_nv, 256)
+        b.upload()
+        b.solve(gq.default_arg(1, prec, ir_fail_ratio=0.0))
+        b.download()
+        torch.cuda.synchronize()
+        fl = b.all_stats()["flags"]
+        assert np.all(fl & gq.FLAG_ARRAY_QR), fl
+        if prec == 1:
+            assert np.all(fl & gq.FLAG_FP64_FALLBACK), fl
         _check_converged(b, qps, refs)
