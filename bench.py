@@ -304,14 +304,14 @@ def condensed_run(qps, block: int, dev, precision: int, reps: int = 3):
             "iters_mean": float(np.mean(st["iters"])), "warp_qps": int(sch.warp_qps), "block_qps": int(sch.block_qps)}
 
 
-def batch_run(qps, dev, precision: int, reps: int = 2):
+def batch_run(qps, dev, precision: int, reps: int = 2, mode: int = 0):
     """Device-timed solves of one batch in one call (inputs resident)."""
     import numpy as np
     import torch
     from paper_2003_02547_gb300 import gq
     from paper_2003_02547_gb300.batch import QpBatch
     b = QpBatch(qps, device=dev)
-    arg = gq.default_arg(gq.MODE_SPEED, precision)
+    arg = gq.default_arg(mode, precision)
     b.upload()
     b.solve(arg)
     torch.cuda.synchronize()
@@ -329,6 +329,8 @@ def batch_run(qps, dev, precision: int, reps: int = 2):
     out = {"value": len(qps) / (min(ms) * 1e-3), "unit": UNIT, "ms": min(ms), "qps": len(qps),
            "converged": int(np.sum(st["status"] == 0)), "iters_mean": float(np.mean(st["iters"])),
            "fp64_fallback_qps": int(np.sum(st["flags"] & gq.FLAG_FP64_FALLBACK != 0))}
+    if mode == gq.MODE_BALANCE:
+        out["array_qr_qps"] = int(np.sum(st["flags"] & gq.FLAG_ARRAY_QR != 0))
     del b
     torch.cuda.empty_cache()
     return out
@@ -338,7 +340,7 @@ def batch_run(qps, dev, precision: int, reps: int = 2):
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; summary in
 # profiles/).  It is reported only while the kernel sources hash to the
 # value recorded with the capture; after any change it reads null.
-TRAFFIC_CAPTURE = {"sha256": "1abd83f291bddd36c93945c79314812a34767adae8a93ef8179d902028baade8", "bytes": 6016754000}
+TRAFFIC_CAPTURE = {"sha256": "399e06e677ddc368d80349f1ce2373efd5c8feedbc4345c9fc47c8fdfb577c30", "bytes": 6034323000}
 KERNEL_SOURCES = ["gq_warp.cu", "gq_device.h", "gq_internal.h", "gq_launch.h", "gq_mma.h"]
 
 
@@ -531,6 +533,19 @@ def main():
     if rank == 0 and world == 1 and not a.no_extras:
         del singles
         extras["mass_spring_condensed_2_mixed"] = condensed_run(qps, 2, dev, gq.PREC_MIXED)
+        # the solver modes of Sec. 4.2 on the same batch (the paper compares
+        # speed and robust on this model): time per solve relative to speed
+        modes = {}
+        for name, mode, prec in (("speed_fp64", gq.MODE_SPEED, gq.PREC_FP64),
+                                 ("balance_fp64", gq.MODE_BALANCE, gq.PREC_FP64),
+                                 ("robust_fp64", gq.MODE_ROBUST, gq.PREC_FP64),
+                                 ("speed_mixed", gq.MODE_SPEED, gq.PREC_MIXED),
+                                 ("robust_mixed", gq.MODE_ROBUST, gq.PREC_MIXED)):
+            modes[name] = batch_run(qps, dev, prec, mode=mode)
+        for name in ("balance_fp64", "robust_fp64"):
+            modes[name]["time_vs_speed"] = modes[name]["ms"] / modes["speed_fp64"]["ms"]
+        modes["robust_mixed"]["time_vs_speed"] = modes["robust_mixed"]["ms"] / modes["speed_mixed"]["ms"]
+        extras["mass_spring_modes"] = modes
         extras["single_small_qp_mixed"] = single_qp_latency(dev, gq.PREC_MIXED)
         extras["single_small_qp_fp64"] = single_qp_latency(dev, gq.PREC_FP64)
         extras["single_small_qp_mixed_graph"] = single_qp_latency(dev, gq.PREC_MIXED, graph=True)
