@@ -8,7 +8,12 @@ What it computes, and the passages it follows (HPIPM paper, arXiv 2003.02547):
 
 * ``assemble``      -- the OCP QP of Sec. 2.2 written out as the generic QP of
                        Sec. 3.1, eq. (qp):  min 1/2 y'Hy + g'y  s.t.  Ay = b,
-                       Cy >= d.  Stage variables are y_n = [u_n; x_n].
+                       Cy >= d.  Stage variables are y_n = [u_n; x_n; s^l_n;
+                       s^u_n]: the slacks of the soft constraints (Sec. 2.2)
+                       are ordinary primal variables here, with their
+                       diagonal costs in H and g, a +1 entry in the side rows
+                       they relax, and sides of their own for s >= lower
+                       bound.  (The CUDA path eliminates them instead.)
 * ``residuals``     -- the residual function of eq. (delta) (r_g, r_b, r_d, r_m)
                        with the Lagrangian sign convention of Sec. 3.1.
 * ``newton_step``   -- eq. (delta) solved by eliminating dt then dlam (Sec. 3.3)
@@ -32,6 +37,10 @@ through code):
   general rows D u + C x], nc_n entries, and lambda/t hold the nc_n lower
   sides followed by the nc_n upper sides.  A side with an infinite bound is
   masked: it is left out of the arithmetic and reported as lambda = 0, t = 1.
+* Soft constraints (Sec. 2.2): slack k of stage n relaxes constraint
+  idxs_n[k]: its lower side becomes c(y) + s^l_k - lo >= 0 and its upper
+  side hi - c(y) + s^u_k >= 0.  After the 2 nc_n constraint sides come ns_n
+  sides s^l_k - lls_k >= 0 and then ns_n sides s^u_k - lus_k >= 0.
 
 Readings where the paper is silent (the same in the CUDA path):
 
@@ -97,17 +106,23 @@ class DenseQp:
     side_off: list = field(default_factory=list)
 
 
+def _ns(qp, n: int) -> int:
+    idxs = getattr(qp, "idxs", None)
+    return 0 if idxs is None else len(idxs[n])
+
+
 def assemble(qp) -> DenseQp:
     """Write the stage-wise OCP QP (Sec. 2.2) as one dense generic QP."""
     N = qp.N
-    nv = [qp.nx[n] + qp.nu[n] for n in range(N + 1)]
+    ns = [_ns(qp, n) for n in range(N + 1)]
+    nv = [qp.nx[n] + qp.nu[n] + 2 * ns[n] for n in range(N + 1)]
     var_off = np.concatenate([[0], np.cumsum(nv)]).astype(int)
     ny = int(var_off[-1])
     eq_sz = [qp.nx[n + 1] for n in range(N)]
     eq_off = np.concatenate([[0], np.cumsum(eq_sz)]).astype(int)
     neq = int(eq_off[-1])
     nc = [qp.nbu(n) + qp.nbx(n) + qp.ng(n) for n in range(N + 1)]
-    side_off = np.concatenate([[0], np.cumsum([2 * c for c in nc])]).astype(int)
+    side_off = np.concatenate([[0], np.cumsum([2 * nc[n] + 2 * ns[n] for n in range(N + 1)])]).astype(int)
     nside = int(side_off[-1])
 
     H = np.zeros((ny, ny))
@@ -120,6 +135,13 @@ def assemble(qp) -> DenseQp:
         H[o + nu:o + nu + nx, o + nu:o + nu + nx] = qp.Q[n]
         g[o:o + nu] = qp.r[n]
         g[o + nu:o + nu + nx] = qp.q[n]
+        for k in range(ns[n]):
+            # slack costs 1/2 Z s^2 + z s, s^l block then s^u block
+            jl, ju = o + nu + nx + k, o + nu + nx + ns[n] + k
+            H[jl, jl] = qp.Zl[n][k]
+            H[ju, ju] = qp.Zu[n][k]
+            g[jl] = qp.zl[n][k]
+            g[ju] = qp.zu[n][k]
 
     A = np.zeros((neq, ny))
     b = np.zeros(neq)
@@ -169,6 +191,20 @@ def assemble(qp) -> DenseQp:
             Crow[s + c + k] = -rows[k]
             dfull[s + c + k] = -hi[k]
             active[s + c + k] = np.isfinite(hi[k])
+        m = ns[n]
+        for k in range(m):
+            # slack k relaxes both sides of constraint idxs[k] and has a
+            # lower bound of its own on each
+            ci = int(qp.idxs[n][k])
+            jl, ju = o + nu + qp.nx[n] + k, o + nu + qp.nx[n] + m + k
+            Crow[s + ci, jl] = 1.0
+            Crow[s + c + ci, ju] = 1.0
+            Crow[s + 2 * c + k, jl] = 1.0
+            dfull[s + 2 * c + k] = qp.lls[n][k]
+            active[s + 2 * c + k] = True
+            Crow[s + 2 * c + m + k, ju] = 1.0
+            dfull[s + 2 * c + m + k] = qp.lus[n][k]
+            active[s + 2 * c + m + k] = True
     return DenseQp(H=H, g=g, A=A, b=b, C=Crow[active], d=dfull[active], active=active,
                    ny=ny, neq=neq, nside=nside, var_off=list(var_off),
                    eq_off=list(eq_off), side_off=list(side_off))
@@ -382,6 +418,16 @@ def duality_gap(dq: DenseQp, y, pi, lam_act) -> float:
     -1/2 y'Hy + b'pi + d'lam (valid where Hy + g - A'pi - C'lam = 0)."""
     dual = -0.5 * float(y @ dq.H @ y) + float(dq.b @ pi) + float(dq.d @ lam_act)
     return objective(dq, y) - dual
+
+
+def split_slacks(qp, dq: DenseQp, y):
+    """y -> list of (s^l_n, s^u_n)."""
+    out = []
+    for n in range(qp.N + 1):
+        o = dq.var_off[n] + qp.nu[n] + qp.nx[n]
+        m = _ns(qp, n)
+        out.append((y[o:o + m], y[o + m:o + 2 * m]))
+    return out
 
 
 def split_stages(qp, dq: DenseQp, y):

@@ -70,9 +70,24 @@ class OcpQp:
     x0: Optional[np.ndarray] = None
     stage_key: List[object] = field(default_factory=list)
     name: str = ""
+    # soft constraints (Sec. 2.2): idxs[n] (ns_n,) indexes the stage's
+    # constraint list [box u; box x; general]; slack k relaxes the lower side
+    # of constraint idxs[n][k] by s^l_k and its upper side by s^u_k, with
+    # cost 1/2 Zl s^l^2 + zl s^l (Zu, zu for s^u) and s^l >= lls, s^u >= lus.
+    # None: no slacks.
+    idxs: Optional[List[np.ndarray]] = None
+    Zl: Optional[List[np.ndarray]] = None
+    Zu: Optional[List[np.ndarray]] = None
+    zl: Optional[List[np.ndarray]] = None
+    zu: Optional[List[np.ndarray]] = None
+    lls: Optional[List[np.ndarray]] = None
+    lus: Optional[List[np.ndarray]] = None
 
     def ng(self, n: int) -> int:
         return self.C[n].shape[0]
+
+    def ns(self, n: int) -> int:
+        return 0 if self.idxs is None else len(self.idxs[n])
 
     def nbu(self, n: int) -> int:
         return len(self.idxbu[n])
@@ -107,6 +122,15 @@ class OcpQp:
                 assert 0 <= min(self.idxbu[n]) and max(self.idxbu[n]) < nu
             if len(self.idxbx[n]):
                 assert 0 <= min(self.idxbx[n]) and max(self.idxbx[n]) < nx
+            ns = self.ns(n)
+            if ns:
+                nc = self.nbu(n) + self.nbx(n) + ng
+                idx = np.asarray(self.idxs[n])
+                assert 0 <= idx.min() and idx.max() < nc and len(set(idx.tolist())) == ns
+                for arr in (self.Zl, self.Zu, self.zl, self.zu, self.lls, self.lus):
+                    assert np.asarray(arr[n]).shape == (ns,)
+                assert np.all(np.asarray(self.Zl[n]) >= 0) and np.all(np.asarray(self.Zu[n]) >= 0)
+                assert np.all(np.isfinite(self.lls[n])) and np.all(np.isfinite(self.lus[n]))
 
 
 def _rng(cfg: int, index: int, redraw: int = 0) -> np.random.Generator:
@@ -368,6 +392,37 @@ def serving_arrivals(rate: float = 20000.0, duration: float = 1.0, repeat_frac: 
             keys.append(key)
             out.append(Arrival(t, key, qp, False))
     return out
+
+
+def soften(qp: OcpQp, stages, which: str = "x", Z: float = 1.0, z: float = 1.0, ls: float = 0.0) -> OcpQp:
+    """Copy of ``qp`` whose constraints of kind ``which`` ("u": boxes on u,
+    "x": boxes on x, "g": general rows, "all") at ``stages`` are soft, with
+    Zl = Zu = Z, zl = zu = z and slack lower bounds ls (Sec. 2.2)."""
+    import copy
+    new = copy.copy(qp)
+    N = qp.N
+    idxs, Zl, Zu, zl, zu, lls, lus = ([np.zeros(0, dtype=np.int32) if k == 0 else np.zeros(0)
+                                       for _ in range(N + 1)] for k in range(7))
+    for n in stages:
+        nbu, nbx, ng = qp.nbu(n), qp.nbx(n), qp.ng(n)
+        sel = []
+        if which in ("u", "all"):
+            sel += list(range(nbu))
+        if which in ("x", "all"):
+            sel += list(range(nbu, nbu + nbx))
+        if which in ("g", "all"):
+            sel += list(range(nbu + nbx, nbu + nbx + ng))
+        m = len(sel)
+        idxs[n] = np.array(sel, dtype=np.int32)
+        Zl[n], Zu[n] = np.full(m, float(Z)), np.full(m, float(Z))
+        zl[n], zu[n] = np.full(m, float(z)), np.full(m, float(z))
+        lls[n], lus[n] = np.full(m, float(ls)), np.full(m, float(ls))
+    new.idxs, new.Zl, new.Zu, new.zl, new.zu, new.lls, new.lus = idxs, Zl, Zu, zl, zu, lls, lus
+    new.name = qp.name + f"_soft{which}"
+    new.stage_key = [(k, "soft", which, float(Z), float(z), float(ls)) if n in set(stages) else k
+                     for n, k in enumerate(qp.stage_key)] if qp.stage_key else []
+    new.validate()
+    return new
 
 
 def perturb_x0(qp: OcpQp, x0_new: np.ndarray) -> OcpQp:
