@@ -166,9 +166,9 @@ typedef struct gq_sizes {
     size_t ws_bytes;       /* device workspace                                     */
     int64_t n_stages;      /* total stages over the batch                          */
     int64_t n_slots;       /* distinct stage data blocks                           */
-    int64_t nv_total;      /* sum of nu_n + nx_n over the batch                    */
+    int64_t nv_total;      /* sum of nu_n + nx_n + 2 ns_n over the batch           */
     int64_t neq_total;     /* sum of nx_{n+1}                                      */
-    int64_t nside_total;   /* sum of 2 (nbu_n + nbx_n + ng_n)                      */
+    int64_t nside_total;   /* sum of 2 (nbu_n + nbx_n + ng_n + ns_n)               */
     int32_t nv_max;        /* largest stage nu_n + nx_n                            */
     int32_t nx_max;        /* largest stage nx_n                                   */
 } gq_sizes;
@@ -187,6 +187,23 @@ GQ_API size_t gq_batch_memsize(int nqp, const int* dims, size_t dims_len, const 
  * while `mem` does; there is no destroy call. */
 GQ_API int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_slot,
                     void* mem, size_t mem_bytes, gq_batch** out);
+
+/* Soft constraints (Sec. 2.2).  As gq_batch_create, plus stage_ns (may be
+ * NULL: no slacks): one int per stage in the order of stage_slot, the number
+ * ns_n (0 <= ns_n <= nc_n) of constraints of that stage made soft.  Slack
+ * pair k of stage n relaxes constraint idxs_n[k] of the stage's list [box
+ * on u; box on x; general rows]: its lower side becomes c + s^l_k >= lo and
+ * its upper side c - s^u_k <= hi, with s^l_k >= lls_k, s^u_k >= lus_k and
+ * the cost 1/2 Zl_k (s^l_k)^2 + zl_k s^l_k + 1/2 Zu_k (s^u_k)^2 + zu_k s^u_k.
+ * With slacks, a stage's block of the y vector is [u; x; s^l; s^u] and its
+ * block of lambda and t is [lower sides (nc); upper sides (nc); bounds of
+ * s^l (ns); bounds of s^u (ns)].  Stages sharing a slot must have equal ns.
+ * The slacks are eliminated inside the solver (a diagonal elimination at
+ * linear cost folded into the barrier terms).  Partial condensing rejects
+ * QPs with slacks (GQ_ERR_ARG).  Errors: those of gq_batch_create, and
+ * GQ_ERR_DIMS for ns_n outside [0, nc_n]. */
+GQ_API int gq_batch_create_soft(int nqp, const int* dims, size_t dims_len, const int* stage_slot,
+                                const int* stage_ns, void* mem, size_t mem_bytes, gq_batch** out);
 
 GQ_API int gq_batch_sizes(const gq_batch* b, gq_sizes* out);
 
@@ -211,9 +228,16 @@ GQ_API int gq_set_box(gq_batch* b, int qp, int n, const int* idxbu, const double
 /* C: ng_n x nx_n, D: ng_n x nu_n, lg, ug: ng_n. */
 GQ_API int gq_set_general(gq_batch* b, int qp, int n, const double* C, int ldc, const double* D, int ldd,
                    const double* lg, const double* ug);
+/* Slack data of stage n (ns_n entries each; nothing to do when ns_n = 0):
+ * idxs distinct constraint indices in [0, nc_n), Zl, Zu >= 0 and finite,
+ * zl, zu, lls, lus finite.  Errors: GQ_ERR_ARG (NULL pointer, index out of
+ * range or repeated), GQ_ERR_DATA (invalid values). */
+GQ_API int gq_set_soft(gq_batch* b, int qp, int n, const int* idxs, const double* Zl, const double* Zu,
+                       const double* zl, const double* zu, const double* lls, const double* lus);
 
-/* Writes an initial guess for QP qp into host_sol (y: sum nv entries in stage
- * order [u_0; x_0; u_1; ...], pi: sum nx_{n+1}, lam/t: sum 2 nc_n; any may be
+/* Writes an initial guess for QP qp into host_sol (y: sum nv + 2 ns entries in
+ * stage order [u_0; x_0; s^l_0; s^u_0; u_1; ...], pi: sum nx_{n+1}, lam/t:
+ * sum 2 (nc_n + ns_n); any may be
  * NULL to leave that part unchanged).  Used with arg.warm_start after
  * gq_upload_sol. */
 GQ_API int gq_set_guess(gq_batch* b, int qp, const double* y, const double* pi,
@@ -251,6 +275,9 @@ GQ_API int gq_get_box(gq_batch* b, int qp, int n, int* idxbu, double* lbu, doubl
                       double* ubx);
 GQ_API int gq_get_general(gq_batch* b, int qp, int n, double* C, int ldc, double* D, int ldd, double* lg,
                           double* ug);
+/* The slack data of gq_set_soft (ns_out receives ns_n; arrays ns_n long). */
+GQ_API int gq_get_soft(gq_batch* b, int qp, int n, int* ns_out, int* idxs, double* Zl, double* Zu, double* zl,
+                       double* zu, double* lls, double* lus);
 
 /* Initial state by elimination (Sec. 2.2 allows stage-wise sizes, so x_0 can
  * be removed: nx_0 = 0).  Stage 0 of QP `qp` must have nx_0 = 0; given the
@@ -344,9 +371,11 @@ GQ_API int gq_solve_noalloc(gq_batch* b, const gq_ipm_arg* arg, void* dev_in, vo
 
 /* ---- getters (read host_sol after gq_download + stream sync) ---- */
 /* u: nu_n, x: nx_n, pi: nx_{n+1} (n < N; multiplier of dynamics block n),
- * lam, t: 2 nc_n.  Any pointer may be NULL. */
+ * lam, t: 2 (nc_n + ns_n).  Any pointer may be NULL. */
 GQ_API int gq_get_stage_sol(const gq_batch* b, int qp, int n, double* u, double* x, double* pi,
                      double* lam, double* t);
+/* sl, su: the ns_n slacks s^l, s^u of stage n (either may be NULL). */
+GQ_API int gq_get_stage_slacks(const gq_batch* b, int qp, int n, double* sl, double* su);
 GQ_API int gq_get_stats(const gq_batch* b, int qp, gq_stats* out);
 /* Offsets (in doubles) of QP qp's vectors inside the sol buffer:
  * off[0] y, off[1] pi, off[2] lam, off[3] t, and their lengths off[4..7]. */

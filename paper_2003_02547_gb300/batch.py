@@ -37,6 +37,13 @@ def dims_of(qps: Sequence) -> np.ndarray:
     return np.array(out, dtype=np.int32)
 
 
+def ns_of(qps: Sequence) -> Optional[np.ndarray]:
+    """Slack pairs per stage (soft constraints, Sec. 2.2), or None if no QP
+    has any."""
+    out = [qp.ns(n) if hasattr(qp, "ns") else 0 for qp in qps for n in range(qp.N + 1)]
+    return np.array(out, dtype=np.int32) if any(out) else None
+
+
 def slots_of(qps: Sequence) -> np.ndarray:
     """Stages whose ``stage_key`` is equal (and not None) share a data block."""
     ids: Dict[object, int] = {}
@@ -95,12 +102,14 @@ class QpBatch:
             self.nqp = len(dims)
             self.dims = np.ascontiguousarray(np.concatenate([np.asarray(d, dtype=np.int32) for d in dims]))
             self.slots = None
+            self.stage_ns = None
             set_data = False
         else:
             self.qps = list(qps)
             self.nqp = len(self.qps)
             self.dims = dims_of(self.qps)
             self.slots = slots_of(self.qps) if share else None
+            self.stage_ns = ns_of(self.qps)
         slot_p = _ptr(self.slots, ctypes.c_int) if self.slots is not None else None
         mem = self.lib.gq_batch_memsize(self.nqp, _ptr(self.dims, ctypes.c_int), self.dims.size, slot_p)
         if mem == 0:
@@ -109,8 +118,9 @@ class QpBatch:
         base = self._hmem.ctypes.data
         self._hmem_ptr = base + ((-base) % 64)
         h = ctypes.c_void_p()
-        gq.check(self.lib.gq_batch_create(self.nqp, _ptr(self.dims, ctypes.c_int), self.dims.size, slot_p,
-                                          self._hmem_ptr, mem, ctypes.byref(h)))
+        ns_p = _ptr(self.stage_ns, ctypes.c_int) if self.stage_ns is not None else None
+        gq.check(self.lib.gq_batch_create_soft(self.nqp, _ptr(self.dims, ctypes.c_int), self.dims.size, slot_p,
+                                               ns_p, self._hmem_ptr, mem, ctypes.byref(h)))
         self.h = h
         self.sizes = gq.Sizes()
         gq.check(self.lib.gq_batch_sizes(self.h, ctypes.byref(self.sizes)))
@@ -161,6 +171,10 @@ class QpBatch:
                 C, D = _f64(qp.C[n]), _f64(qp.D[n])
                 gq.check(L.gq_set_general(h, i, n, _ptr(C), ng, _ptr(D), ng, _ptr(_f64(qp.lg[n])),
                                           _ptr(_f64(qp.ug[n]))))
+            if hasattr(qp, "ns") and qp.ns(n):
+                gq.check(L.gq_set_soft(h, i, n, _ptr(_i32(qp.idxs[n]), ctypes.c_int), _ptr(_f64(qp.Zl[n])),
+                                       _ptr(_f64(qp.Zu[n])), _ptr(_f64(qp.zl[n])), _ptr(_f64(qp.zu[n])),
+                                       _ptr(_f64(qp.lls[n])), _ptr(_f64(qp.lus[n]))))
 
     def _stage_base(self, i: int) -> int:
         if not hasattr(self, "_sbase"):
@@ -200,6 +214,7 @@ class QpBatch:
         PI = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
         out = {k: [] for k in ("A", "B", "b", "Q", "S", "R", "q", "r", "idxbu", "lbu", "ubu", "idxbx", "lbx", "ubx",
                                "C", "D", "lg", "ug")}
+        soft: dict = {}
         for n in range(N + 1):
             x, u, nbx, nbu, ng = sd[n]
             if n < N:
@@ -231,6 +246,16 @@ class QpBatch:
             out["D"].append(D[:ng, :u].copy())
             out["lg"].append(lg[:ng].copy())
             out["ug"].append(ug[:ng].copy())
+            nsv = ctypes.c_int()
+            gq.check(L.gq_get_soft(h, i, n, ctypes.byref(nsv), None, None, None, None, None, None, None))
+            ns = nsv.value
+            arrs = [np.zeros(max(ns, 1), dtype=np.int32)] + [np.zeros(max(ns, 1)) for _ in range(6)]
+            if ns:
+                gq.check(L.gq_get_soft(h, i, n, None, PI(arrs[0]), *[P(a) for a in arrs[1:]]))
+            for key, a in zip(("idxs", "Zl", "Zu", "zl", "zu", "lls", "lus"), arrs):
+                soft.setdefault(key, []).append(a[:ns].copy())
+        if any(len(v) for v in soft.get("idxs", [])):
+            out.update(soft)
         qp = OcpQp(N=N, nx=nx, nu=nu, **out)
         qp.validate()
         return qp

@@ -5,6 +5,7 @@ Compiles every translation unit of csrc/ in parallel with nvcc and links
 """
 import concurrent.futures as cf
 import os
+import re
 import subprocess
 import sys
 
@@ -27,10 +28,21 @@ def sources():
     return sorted(os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".cu"))
 
 
+def _included_sources(src):
+    """Other .cu files a translation unit includes (a kernel built twice)."""
+    out = []
+    with open(src) as fh:
+        for line in fh:
+            m = re.match(r'\s*#include\s+"([^"]+\.cu)"', line)
+            if m:
+                out.append(os.path.join(SRC, m.group(1)))
+    return out
+
+
 def _compile(src):
     obj = os.path.join(OUT, os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(
-            os.path.getmtime(p) for p in [src] + _headers()):
+            os.path.getmtime(p) for p in [src] + _included_sources(src) + _headers()):
         return obj
     cmd = [_nvcc()] + ARCH + FLAGS + ["-I", os.path.join(HERE, "..", "include"), "-c", src, "-o", obj]
     subprocess.run(cmd, check=True)

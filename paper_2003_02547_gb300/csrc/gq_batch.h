@@ -30,6 +30,7 @@ struct gq_batch {
   gq_sizes sizes;
   int32_t ngmax;
   int32_t nwarp;        // QPs run one per warp; they lead the order array
+  int32_t soft_block;   // 1: some QP of the block bucket has slacks (launch the soft kernel variant)
   int32_t warp_max_nv;  // schedule: largest nu + nx (and nx) of a QP run one per warp
   int32_t block_threads;  // schedule: threads per block of the block kernel
   gq::Shape shape_w, shape_b;

@@ -155,6 +155,13 @@ void t_row(const BlockMaps& m, int j, int nu, int r, std::vector<double>* row) {
   }
 }
 
+bool has_slacks(const gq_batch* b, int qp) {
+  const gq::QpDesc& d = b->qp[qp];
+  for (int n = 0; n <= d.N; ++n)
+    if (b->st[d.stage0 + n].ns > 0) return true;
+  return false;
+}
+
 int read_block(gq_batch* src, int qp, int N, int n0, int n1, std::vector<StageData>* st) {
   st->resize((size_t)(n1 - n0 + 1));
   for (int n = n0; n <= n1; ++n) {
@@ -172,6 +179,7 @@ int gq_condense_dims(const gq_batch* src, int qp, int block, int* dims, size_t c
   if (src == nullptr || len == nullptr) return set_error(GQ_ERR_ARG, "NULL argument");
   if (qp < 0 || qp >= src->nqp) return set_error(GQ_ERR_ARG, "qp out of range");
   if (block < 1) return set_error(GQ_ERR_ARG, "block must be >= 1");
+  if (has_slacks(src, qp)) return set_error(GQ_ERR_ARG, "condensing of QPs with soft constraints is not supported");
   const int N = src->qp[qp].N;
   const int N2 = condensed_horizon(N, block);
   const size_t need = 1 + 5 * (size_t)(N2 + 1);
@@ -211,6 +219,8 @@ int gq_condense(gq_batch* src, int src_qp, int block, gq_batch* dst, int dst_qp)
   if (src_qp < 0 || src_qp >= src->nqp || dst_qp < 0 || dst_qp >= dst->nqp)
     return set_error(GQ_ERR_ARG, "QP index out of range");
   if (block < 1) return set_error(GQ_ERR_ARG, "block must be >= 1");
+  if (has_slacks(src, src_qp))
+    return set_error(GQ_ERR_ARG, "condensing of QPs with soft constraints is not supported");
   const int N = src->qp[src_qp].N;
   const int N2 = condensed_horizon(N, block);
   if (dst->qp[dst_qp].N != N2) return set_error(GQ_ERR_DIMS, "destination horizon %d != %d", dst->qp[dst_qp].N, N2);

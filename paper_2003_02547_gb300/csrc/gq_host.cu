@@ -202,7 +202,7 @@ Shape bucket_shape(const gq_batch* b, int lo, int hi, bool all) {
       sh.nxmax = std::max(sh.nxmax, st.nx);
       sh.ngmax = std::max(sh.ngmax, st.ng);
       sh.ne_max = std::max(sh.ne_max, n == 0 ? nv : st.nu);
-      sh.data_max = std::max(sh.data_max, stage_data_layout(st.nx, st.nu, st.nx1, st.nbu + st.nbx, st.ng).size);
+      sh.data_max = std::max(sh.data_max, stage_data_layout(st).size);
     }
   }
   return sh;
@@ -215,7 +215,9 @@ void plan_buckets(gq_batch* b) {
   const int nqp = b->nqp;
   const QpDesc* qd = b->qp;
   const int wmax = b->warp_max_nv;
-  auto warp_ok = [&](int q) { return qd[q].nvmax <= wmax && qd[q].nxmax <= wmax; };
+  // the one-warp kernel has no slack elimination: QPs with soft constraints
+  // run in the block kernel
+  auto warp_ok = [&](int q) { return qd[q].nvmax <= wmax && qd[q].nxmax <= wmax && qd[q].nsoft == 0; };
   int nw = 0;
   for (int q = 0; q < nqp; ++q)
     if (warp_ok(q)) b->order[nw++] = q;
@@ -226,6 +228,8 @@ void plan_buckets(gq_batch* b) {
   std::stable_sort(b->order, b->order + nw, by_cost);
   std::stable_sort(b->order + nw, b->order + nqp, by_cost);
   b->nwarp = nw;
+  b->soft_block = 0;
+  for (int i = nw; i < nqp; ++i) b->soft_block |= qd[b->order[i]].nsoft > 0;
   b->shape_w = bucket_shape(b, 0, nw, false);
   b->shape_b = bucket_shape(b, nw, nqp, false);
   if (nqp > nw) b->shape_b.mat_global = 1;
@@ -245,6 +249,11 @@ size_t gq_batch_memsize(int nqp, const int* dims, size_t dims_len, const int* st
 
 int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_slot, void* mem,
                     size_t mem_bytes, gq_batch** out) {
+  return gq_batch_create_soft(nqp, dims, dims_len, stage_slot, nullptr, mem, mem_bytes, out);
+}
+
+int gq_batch_create_soft(int nqp, const int* dims, size_t dims_len, const int* stage_slot, const int* stage_ns,
+                         void* mem, size_t mem_bytes, gq_batch** out) {
   if (out == nullptr || mem == nullptr) return fail(GQ_ERR_ARG, "mem and out must be non-NULL");
   *out = nullptr;
   if (reinterpret_cast<uintptr_t>(mem) % 16) return fail(GQ_ERR_ARG, "mem must be 16-byte aligned");
@@ -299,13 +308,17 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
       s.ng = dn[4];
       s.nx1 = (n < N) ? dims[pos + 5 * (n + 1)] : 0;
       const int nv = s.nx + s.nu, nb = s.nbx + s.nbu, nc = nb + s.ng;
+      s.ns = stage_ns ? stage_ns[si] : 0;
+      if (s.ns < 0 || s.ns > nc)
+        return fail(GQ_ERR_DIMS, "QP %d stage %d: %d slacks for %d constraints", q, n, s.ns, nc);
       s.var = (int32_t)var;
       s.eq = (int32_t)eq;
       s.side = (int32_t)side;
       s.fac = fac;
-      var += nv;
+      var += nv + 2 * s.ns;
+      d.nsoft += s.ns;
       eq += s.nx1;
-      side += 2 * nc;
+      side += 2 * nc + 2 * s.ns;
       fac += fac_block_elems(nv);
       nvmax = std::max(nvmax, nv);
       nxmax = std::max(nxmax, s.nx);
@@ -315,10 +328,9 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
       d.nxmax = std::max(d.nxmax, s.nx);
       cost += (double)s.nx1 * s.nx1 * nv + (double)s.nx1 * nv * nv + (double)nv * nv * nv / 3.0 +
               (double)s.ng * nv * nv;
-      const StageData lay = stage_data_layout(s.nx, s.nu, s.nx1, nb, s.ng);
+      const StageData lay = stage_data_layout(s);
       datamax = std::max(datamax, lay.size);
       const int slot = stage_slot ? stage_slot[si] : -1;
-      s.idx = 0;
       if (slot < 0) {
         s.data = data;
         data += lay.size;
@@ -336,7 +348,7 @@ int gq_batch_create(int nqp, const int* dims, size_t dims_len, const int* stage_
         } else {
           const StageDesc& f = b->st[b->hash[h].stage];
           if (f.nx != s.nx || f.nu != s.nu || f.nx1 != s.nx1 || f.nbx != s.nbx || f.nbu != s.nbu ||
-              f.ng != s.ng)
+              f.ng != s.ng || f.ns != s.ns)
             return fail(GQ_ERR_DIMS, "QP %d stage %d shares slot %d with a stage of other sizes", q, n,
                         slot);
           s.data = b->hash[h].block;
@@ -474,7 +486,7 @@ int gq_set_dynamics(gq_batch* b, int qp, int n, const double* A, int lda, const 
   if ((nx && A == nullptr) || (nu && B == nullptr) || bvec == nullptr)
     return fail(GQ_ERR_ARG, "dynamics pointers must be non-NULL");
   if ((nx && lda < nx1) || (nu && ldb < nx1)) return fail(GQ_ERR_ARG, "leading dimension too small");
-  const StageData lay = stage_data_layout(nx, nu, nx1, s->nbu + s->nbx, s->ng);
+  const StageData lay = stage_data_layout(*s);
   double* D = host_data(b) + s->data;
   for (int i = 0; i < nu; ++i)
     for (int k = 0; k < nx1; ++k) D[lay.BAt + (int64_t)i * lay.ldb + k] = B[k + (int64_t)i * ldb];
@@ -506,7 +518,7 @@ int gq_set_cost(gq_batch* b, int qp, int n, const double* Q, int ldq, const doub
       const double a = R[i + (int64_t)j * ldr], c = R[j + (int64_t)i * ldr];
       if (!(std::fabs(a - c) <= 1e-12 * (1.0 + std::fabs(a)))) return fail(GQ_ERR_DATA, "R not symmetric");
     }
-  const StageData lay = stage_data_layout(nx, nu, s->nx1, s->nbu + s->nbx, s->ng);
+  const StageData lay = stage_data_layout(*s);
   double* D = host_data(b) + s->data;
   double* RSQ = D + lay.RSQ;
   const int64_t lr = lay.ldr;
@@ -535,7 +547,7 @@ int gq_set_box(gq_batch* b, int qp, int n, const int* idxbu, const double* lbu, 
   if ((nbu && (idxbu == nullptr || lbu == nullptr || ubu == nullptr)) ||
       (nbx && (idxbx == nullptr || lbx == nullptr || ubx == nullptr)))
     return fail(GQ_ERR_ARG, "box pointers must be non-NULL");
-  const StageData lay = stage_data_layout(s->nx, s->nu, s->nx1, nb, s->ng);
+  const StageData lay = stage_data_layout(*s);
   double* D = host_data(b) + s->data;
   int32_t* I = reinterpret_cast<int32_t*>(D + lay.box);   // bidx[nb], then bmap[nv]
   for (int k = 0; k < nbu; ++k) {
@@ -577,7 +589,7 @@ int gq_set_general(gq_batch* b, int qp, int n, const double* C, int ldc, const d
   if ((nx && C == nullptr) || (nu && Dm == nullptr) || lg == nullptr || ug == nullptr)
     return fail(GQ_ERR_ARG, "general-constraint pointers must be non-NULL");
   if ((nx && ldc < ng) || (nu && ldd < ng)) return fail(GQ_ERR_ARG, "leading dimension too small");
-  const StageData lay = stage_data_layout(nx, nu, s->nx1, nb, ng);
+  const StageData lay = stage_data_layout(*s);
   double* D = host_data(b) + s->data;
   for (int g = 0; g < ng; ++g) {
     for (int i = 0; i < nu; ++i) D[lay.DC + (int64_t)g * nv + i] = Dm[g + (int64_t)i * ldd];
@@ -589,6 +601,38 @@ int gq_set_general(gq_batch* b, int qp, int n, const double* C, int ldc, const d
     D[lay.hi + nb + g] = hi;
   }
   if (!finite_all(D + lay.DC, ng * nv)) return fail(GQ_ERR_DATA, "non-finite general-constraint data");
+  return GQ_OK;
+}
+
+int gq_set_soft(gq_batch* b, int qp, int n, const int* idxs, const double* Zl, const double* Zu,
+                const double* zl, const double* zu, const double* lls, const double* lus) {
+  StageDesc* s;
+  int rc = stage_of(b, qp, n, &s);
+  if (rc) return rc;
+  const int ns = s->ns, nb = s->nbu + s->nbx, nc = nb + s->ng, nv = s->nx + s->nu;
+  if (ns == 0) return GQ_OK;
+  if (!idxs || !Zl || !Zu || !zl || !zu || !lls || !lus) return fail(GQ_ERR_ARG, "slack pointers must be non-NULL");
+  const StageData lay = stage_data_layout(*s);
+  double* D = host_data(b) + s->data;
+  int32_t* I = reinterpret_cast<int32_t*>(D + lay.box);
+  int32_t* sidx = I + nb + nv;
+  int32_t* smap = sidx + ns;
+  for (int c = 0; c < nc; ++c) smap[c] = -1;
+  for (int k = 0; k < ns; ++k) {
+    if (idxs[k] < 0 || idxs[k] >= nc) return fail(GQ_ERR_ARG, "idxs[%d]=%d out of range", k, idxs[k]);
+    if (smap[idxs[k]] >= 0) return fail(GQ_ERR_ARG, "idxs has a repeated index %d", idxs[k]);
+    if (!(Zl[k] >= 0.0 && Zu[k] >= 0.0) || !std::isfinite(Zl[k]) || !std::isfinite(Zu[k]) ||
+        !std::isfinite(zl[k]) || !std::isfinite(zu[k]) || !std::isfinite(lls[k]) || !std::isfinite(lus[k]))
+      return fail(GQ_ERR_DATA, "slack %d: Z must be finite and >= 0, z and the slack bounds finite", k);
+    sidx[k] = idxs[k];
+    smap[idxs[k]] = k;
+    D[lay.Zs + k] = Zl[k];
+    D[lay.Zs + ns + k] = Zu[k];
+    D[lay.zs + k] = zl[k];
+    D[lay.zs + ns + k] = zu[k];
+    D[lay.ls + k] = lls[k];
+    D[lay.ls + ns + k] = lus[k];
+  }
   return GQ_OK;
 }
 
@@ -607,7 +651,7 @@ int gq_set_initial_state(gq_batch* b, int qp, const double* x0, int nx0, const d
     return fail(GQ_ERR_ARG, "b0, r0, lg0, ug0 must be non-NULL");
   if (nx0 > 0 && (lda < nx1 || (nu && lds < nu) || (ng && ldc < ng)))
     return fail(GQ_ERR_ARG, "leading dimension too small");
-  const StageData lay = stage_data_layout(0, nu, nx1, nb, ng);
+  const StageData lay = stage_data_layout(*s);
   double* D = host_data(b) + s->data;
   // b_0 + A_0 x0, r_0 + S_0 x0, and the general bounds minus C_0 x0
   for (int k = 0; k < nx1; ++k) {
@@ -643,7 +687,7 @@ int gq_get_dynamics(gq_batch* b, int qp, int n, double* A, int lda, double* B, i
   if (n == b->qp[qp].N) return fail(GQ_ERR_ARG, "stage %d is terminal: no dynamics", n);
   const int nx = s->nx, nu = s->nu, nx1 = s->nx1;
   if ((A && nx && lda < nx1) || (B && nu && ldb < nx1)) return fail(GQ_ERR_ARG, "leading dimension too small");
-  const StageData lay = stage_data_layout(nx, nu, nx1, s->nbu + s->nbx, s->ng);
+  const StageData lay = stage_data_layout(*s);
   const double* D = host_data(b) + s->data;
   for (int i = 0; i < nu && B; ++i)
     for (int k = 0; k < nx1; ++k) B[k + (int64_t)i * ldb] = D[lay.BAt + (int64_t)i * lay.ldb + k];
@@ -661,7 +705,7 @@ int gq_get_cost(gq_batch* b, int qp, int n, double* Q, int ldq, double* S, int l
   const int nx = s->nx, nu = s->nu;
   if ((Q && nx && ldq < nx) || (R && nu && ldr < nu) || (S && nu && nx && lds < nu))
     return fail(GQ_ERR_ARG, "leading dimension too small");
-  const StageData lay = stage_data_layout(nx, nu, s->nx1, s->nbu + s->nbx, s->ng);
+  const StageData lay = stage_data_layout(*s);
   const double* D = host_data(b) + s->data;
   const double* RSQ = D + lay.RSQ;
   const int64_t lr = lay.ldr;
@@ -682,7 +726,7 @@ int gq_get_box(gq_batch* b, int qp, int n, int* idxbu, double* lbu, double* ubu,
   int rc = stage_of(b, qp, n, &s);
   if (rc) return rc;
   const int nbu = s->nbu, nbx = s->nbx, nb = nbu + nbx;
-  const StageData lay = stage_data_layout(s->nx, s->nu, s->nx1, nb, s->ng);
+  const StageData lay = stage_data_layout(*s);
   const double* D = host_data(b) + s->data;
   const int32_t* I = reinterpret_cast<const int32_t*>(D + lay.box);
   for (int k = 0; k < nbu; ++k) {
@@ -704,13 +748,36 @@ int gq_get_general(gq_batch* b, int qp, int n, double* C, int ldc, double* Dm, i
   if (rc) return rc;
   const int ng = s->ng, nx = s->nx, nu = s->nu, nv = nx + nu, nb = s->nbu + s->nbx;
   if ((C && nx && ng && ldc < ng) || (Dm && nu && ng && ldd < ng)) return fail(GQ_ERR_ARG, "leading dimension too small");
-  const StageData lay = stage_data_layout(nx, nu, s->nx1, nb, ng);
+  const StageData lay = stage_data_layout(*s);
   const double* D = host_data(b) + s->data;
   for (int g = 0; g < ng; ++g) {
     for (int i = 0; i < nu && Dm; ++i) Dm[g + (int64_t)i * ldd] = D[lay.DC + (int64_t)g * nv + i];
     for (int i = 0; i < nx && C; ++i) C[g + (int64_t)i * ldc] = D[lay.DC + (int64_t)g * nv + nu + i];
     if (lg) lg[g] = D[lay.lo + nb + g];
     if (ug) ug[g] = D[lay.hi + nb + g];
+  }
+  return GQ_OK;
+}
+
+int gq_get_soft(gq_batch* b, int qp, int n, int* ns_out, int* idxs, double* Zl, double* Zu, double* zl, double* zu,
+                double* lls, double* lus) {
+  StageDesc* s;
+  int rc = stage_of(b, qp, n, &s);
+  if (rc) return rc;
+  const int ns = s->ns, nb = s->nbu + s->nbx, nv = s->nx + s->nu;
+  if (ns_out) *ns_out = ns;
+  if (ns == 0) return GQ_OK;
+  const StageData lay = stage_data_layout(*s);
+  const double* D = host_data(b) + s->data;
+  const int32_t* sidx = reinterpret_cast<const int32_t*>(D + lay.box) + nb + nv;
+  for (int k = 0; k < ns; ++k) {
+    if (idxs) idxs[k] = sidx[k];
+    if (Zl) Zl[k] = D[lay.Zs + k];
+    if (Zu) Zu[k] = D[lay.Zs + ns + k];
+    if (zl) zl[k] = D[lay.zs + k];
+    if (zu) zu[k] = D[lay.zs + ns + k];
+    if (lls) lls[k] = D[lay.ls + k];
+    if (lus) lus[k] = D[lay.ls + ns + k];
   }
   return GQ_OK;
 }
@@ -820,7 +887,8 @@ static cudaError_t launch_all(gq_batch* b, const Batch& k, const gq_ipm_arg& arg
   const int32_t* ord = k.order;
   cudaError_t e = launch_warp_ipm(k, b->shape_w, arg, st, kind, sigma_mu, out, ord, b->nwarp);
   if (e != cudaSuccess) return e;
-  return launch_ipm(k, b->shape_b, arg, st, kind, sigma_mu, out, ord + b->nwarp, b->nqp - b->nwarp);
+  return (b->soft_block ? launch_ipm_soft : launch_ipm)(k, b->shape_b, arg, st, kind, sigma_mu, out, ord + b->nwarp,
+                                                        b->nqp - b->nwarp);
 }
 
 static int check_arg(const gq_ipm_arg* a) {
@@ -991,9 +1059,23 @@ int gq_get_stage_sol(const gq_batch* b, int qp, int n, double* u, double* x, dou
   if (u) std::memcpy(u, Y, 8 * (size_t)s.nu);
   if (x) std::memcpy(x, Y + s.nu, 8 * (size_t)s.nx);
   if (pi && n < d.N) std::memcpy(pi, reinterpret_cast<const double*>(h + b->L.pi) + s.eq, 8 * (size_t)s.nx1);
-  const int ns = 2 * (s.nbu + s.nbx + s.ng);
-  if (lam) std::memcpy(lam, reinterpret_cast<const double*>(h + b->L.lam) + s.side, 8 * (size_t)ns);
-  if (t) std::memcpy(t, reinterpret_cast<const double*>(h + b->L.t) + s.side, 8 * (size_t)ns);
+  const int nside = 2 * (s.nbu + s.nbx + s.ng + s.ns);
+  if (lam) std::memcpy(lam, reinterpret_cast<const double*>(h + b->L.lam) + s.side, 8 * (size_t)nside);
+  if (t) std::memcpy(t, reinterpret_cast<const double*>(h + b->L.t) + s.side, 8 * (size_t)nside);
+  return GQ_OK;
+}
+
+int gq_get_stage_slacks(const gq_batch* b, int qp, int n, double* sl, double* su) {
+  int rc = check_batch(b);
+  if (rc) return rc;
+  if (qp < 0 || qp >= b->nqp) return fail(GQ_ERR_ARG, "qp out of range");
+  const QpDesc& d = b->qp[qp];
+  if (n < 0 || n > d.N) return fail(GQ_ERR_ARG, "stage out of range");
+  if (b->host_sol == nullptr) return fail(GQ_ERR_STATE, "host_sol not attached");
+  const StageDesc& s = b->st[d.stage0 + n];
+  const double* Y = reinterpret_cast<const double*>(static_cast<const char*>(b->host_sol) + b->L.y) + s.var;
+  if (sl) std::memcpy(sl, Y + s.nu + s.nx, 8 * (size_t)s.ns);
+  if (su) std::memcpy(su, Y + s.nu + s.nx + s.ns, 8 * (size_t)s.ns);
   return GQ_OK;
 }
 
@@ -1130,7 +1212,7 @@ extern "C" int gq_copy_qp(gq_batch* dst, int dst_qp, const gq_batch* src, int sr
   for (int n = 0; n <= a.N; ++n) {
     const StageDesc& sa = dst->st[a.stage0 + n];
     const StageDesc& sc = src->st[c.stage0 + n];
-    if (sa.nx != sc.nx || sa.nu != sc.nu || sa.nbx != sc.nbx || sa.nbu != sc.nbu || sa.ng != sc.ng)
+    if (sa.nx != sc.nx || sa.nu != sc.nu || sa.nbx != sc.nbx || sa.nbu != sc.nbu || sa.ng != sc.ng || sa.ns != sc.ns)
       return fail(GQ_ERR_DIMS, "copy_qp: stage %d sizes differ", n);
   }
   const char* sb = static_cast<const char*>(src->host_in) + src->L.data;
@@ -1138,7 +1220,7 @@ extern "C" int gq_copy_qp(gq_batch* dst, int dst_qp, const gq_batch* src, int sr
   for (int n = 0; n <= a.N; ++n) {
     const StageDesc& sa = dst->st[a.stage0 + n];
     const StageDesc& sc = src->st[c.stage0 + n];
-    const StageData lay = stage_data_layout(sa.nx, sa.nu, sa.nx1, sa.nbu + sa.nbx, sa.ng);
+    const StageData lay = stage_data_layout(sa);
     std::memcpy(db + 8 * sa.data, sb + 8 * sc.data, 8 * (size_t)lay.size);
   }
   return GQ_OK;

@@ -8,12 +8,15 @@
 namespace gq {
 
 // One stage of one QP.  Offsets index batch-wide arrays:
-//   var  -> y / dy / r_g / ... (sum of nu+nx),  eq -> pi / r_b (sum of nx_{n+1}),
-//   side -> lambda / t / r_d (sum of 2 nc),     idx -> int arena,
+//   var  -> y / dy / r_g / ... (sum of nu+nx+2ns: [u; x; s^l; s^u]),
+//   eq   -> pi / r_b (sum of nx_{n+1}),
+//   side -> lambda / t / r_d (sum of 2 nc + 2 ns: lower sides, upper sides,
+//           bounds of s^l, bounds of s^u),
+//   ns   -> soft constraints (slack pairs) of the stage (Sec. 2.2),
 //   data -> FP64 stage data block (may be shared), fac -> factor arena element.
 struct StageDesc {
   int32_t nx, nu, nx1, nbu, nbx, ng;
-  int32_t var, eq, side, idx;
+  int32_t var, eq, side, ns;
   int64_t data;
   int64_t fac;
 };
@@ -25,7 +28,7 @@ struct QpDesc {
   int32_t nvt, neqt, nsidet;  // lengths of this QP's vectors
   int32_t nvmax, nxmax;       // largest stage sizes of this QP
   int32_t warm;               // 0: arg.warm_start applies; 1 + level: this QP's own warm-start level
-  int32_t pad1;
+  int32_t nsoft;              // slack pairs over all stages (soft constraints; block kernel only)
   double cost;                // flop estimate of one Riccati factorisation
 };
 static_assert(sizeof(QpDesc) == 56, "QpDesc layout");
@@ -39,8 +42,13 @@ static_assert(sizeof(QpDesc) == 56, "QpDesc layout");
 //   DC   ng x nv row-major, [D C]
 //   lo   nc   (box u, box x, general), -inf masks the side
 //   hi   nc
-//   box  int32 region of nb + nv element slots: bidx[nb] (variable index of
-//        box c within [u;x]) then bmap[nv] (box index of variable i, or -1)
+//   Zs   2 ns, [Zl; Zu]  diagonal slack Hessians      (only when ns > 0)
+//   zs   2 ns, [zl; zu]  slack gradients
+//   ls   2 ns, [lls; lus] lower bounds of s^l, s^u
+//   box  int32 region of nint element slots: bidx[nb] (variable index of
+//        box c within [u;x]) then bmap[nv] (box index of variable i, or -1);
+//        with slacks also sidx[ns] (constraint relaxed by slack k) and
+//        smap[nc] (slack of constraint c, or -1)
 // The same element layout serves the FP64 block and its FP32 mirror (the box
 // region is sized so that its int32 entries fit at either element width).
 // Odd row strides keep lane-per-row shared-memory reads free of bank
@@ -49,10 +57,10 @@ static_assert(sizeof(QpDesc) == 56, "QpDesc layout");
 // (one bulk copy per stage).
 __host__ __device__ inline int odd_ld(int n) { return n | 1; }
 struct StageData {
-  int64_t BAt, b, RSQ, rq, DC, lo, hi, box, size;
-  int ldb, ldr;
+  int64_t BAt, b, RSQ, rq, DC, lo, hi, Zs, zs, ls, box, size;
+  int ldb, ldr, nint;
 };
-__host__ __device__ inline StageData stage_data_layout(int nx, int nu, int nx1, int nb, int ng) {
+__host__ __device__ inline StageData stage_data_layout(int nx, int nu, int nx1, int nb, int ng, int ns) {
   StageData s;
   const int64_t nv = nx + nu, nc = nb + ng;
   s.ldb = odd_ld(nx1);
@@ -64,9 +72,16 @@ __host__ __device__ inline StageData stage_data_layout(int nx, int nu, int nx1, 
   s.DC = s.rq + nv;
   s.lo = s.DC + (int64_t)ng * nv;
   s.hi = s.lo + nc;
-  s.box = s.hi + nc;
-  s.size = (s.box + nb + nv + 3) & ~int64_t(3);
+  s.Zs = s.hi + nc;
+  s.zs = s.Zs + 2 * ns;
+  s.ls = s.zs + 2 * ns;
+  s.box = s.ls + 2 * ns;
+  s.nint = (int)(nb + nv + (ns > 0 ? ns + nc : 0));
+  s.size = (s.box + s.nint + 3) & ~int64_t(3);
   return s;
+}
+__host__ __device__ inline StageData stage_data_layout(const StageDesc& st) {
+  return stage_data_layout(st.nx, st.nu, st.nx1, st.nbu + st.nbx, st.ng, st.ns);
 }
 
 // Factor block of a stage: nv x odd_ld(nv) row-major, padded to a multiple of

@@ -42,6 +42,15 @@
 #include "gq_internal.h"
 #include "gq_launch.h"
 #include "gq_mma.h"
+#include "gq_soft.h"
+
+// Soft constraints (Sec. 2.2): the slack elimination is compiled in only when
+// GQ_IPM_SOFT is 1 (gq_ipm_soft.cu builds this file that way and exports
+// launch_ipm_soft), so that the kernel for QPs without slacks keeps its
+// register allocation; the host picks the variant per batch.
+#ifndef GQ_IPM_SOFT
+#define GQ_IPM_SOFT 0
+#endif
 
 namespace gq {
 
@@ -220,7 +229,7 @@ __device__ __forceinline__ void rows_dot(int nrows, Lo lo, Hi hi, Term term, Out
 }
 
 __device__ __forceinline__ StageData lay(const StageDesc& s) {
-  return stage_data_layout(s.nx, s.nu, s.nx1, s.nbu + s.nbx, s.ng);
+  return stage_data_layout(s);
 }
 __device__ __forceinline__ const int32_t* box_idx(const double* D, const StageData& L) {
   return reinterpret_cast<const int32_t*>(D + L.box);
@@ -358,9 +367,28 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
       double a = 0.0, b = 0.0;
       if (lo != -INFINITY) a = lo - v + t[il];
       if (hi != INFINITY) b = v - hi + t[iu];
+      if (GQ_IPM_SOFT && s.ns > 0) {
+        // a relaxed side's row also holds its slack (Sec. 2.2)
+        const int k = soft::soft_smap(box_idx(D, L), nb, nv, s.ns)[c];
+        if (k >= 0) {
+          if (lo != -INFINITY) a -= yn[nv + k];
+          if (hi != INFINITY) b -= yn[nv + s.ns + k];
+        }
+      }
       rd[il] = a;
       rd[iu] = b;
       mx.d = max_nan(mx.d, max_nan(fabs(a), fabs(b)));
+    }
+  }
+  if (GQ_IPM_SOFT && s.ns > 0) {
+    // slack stationarity rows and the slack bound sides
+    const int32_t* sidx = soft::soft_sidx(box_idx(D, L), nb, nv);
+    for (int k = tid; k < s.ns; k += NT) {
+      const soft::SoftSlot q = soft::soft_slot(s, nv, nc, k, sidx[k]);
+      double sl, su, mg, md;
+      soft::soft_residual(D, L, s.ns, k, q, y, lam, t, og, rd, lin, add_g, &sl, &su, &mg, &md);
+      mx.g = max_nan(mx.g, mg);
+      mx.d = max_nan(mx.d, md);
     }
   }
 }
@@ -430,6 +458,19 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
     if (D[L.lo + c] != -INFINITY) w += lm[c] / tt[c];
     if (D[L.hi + c] != INFINITY) w += lm[nc + c] / tt[nc + c];
     sw[c] = (Tf)w;
+  }
+  if (GQ_IPM_SOFT && s.ns > 0) {
+    // relaxed constraints: their slacks eliminated into the weight (Sec. 2.2)
+    __syncthreads();
+    const int32_t* sidx = soft::soft_sidx(box_idx(D, L), nb, nv);
+    for (int k = tid; k < s.ns; k += NT) {
+      const int c = sidx[k];
+      const soft::SoftSlot q = soft::soft_slot(s, nv, nc, k, c);
+      const soft::SoftElim e = soft::soft_elim(D, L, s.ns, k, q, D[L.lo + c] != -INFINITY, D[L.hi + c] != INFINITY,
+                                               B.lam, B.t, nullptr, nullptr, nullptr);
+      sw[c] = (Tf)soft::soft_weight(e);
+    }
+    __syncthreads();
   }
   if constexpr (sizeof(Tf) == 4) {
     // FP32 factor: both products on the tensor cores (3xTF32 mma.sync), each
@@ -820,6 +861,18 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
         if (D[L.hi + c] != INFINITY) v -= (lm[nc + c] * rd[iu] - rm[iu]) / tt[nc + c];
         vs[c] = v;
       }
+      if (GQ_IPM_SOFT && s.ns > 0) {
+        // relaxed constraints: the eliminated slacks' gradient terms
+        __syncthreads();
+        const int32_t* sidx = soft::soft_sidx(box_idx(D, L), nb, nv);
+        for (int k = tid; k < s.ns; k += NT) {
+          const int c = sidx[k];
+          const soft::SoftSlot q = soft::soft_slot(s, nv, nc, k, c);
+          const soft::SoftElim e = soft::soft_elim(D, L, s.ns, k, q, D[L.lo + c] != -INFINITY,
+                                                   D[L.hi + c] != INFINITY, B.lam, B.t, g, rd, rm);
+          vs[c] += soft::soft_grad(e);
+        }
+      }
     }
     if (n < C.N && !C.classical) {
       // va = L_{n+1}' rb_n
@@ -955,6 +1008,16 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
       } else {
         dt[iu] = 0.0;
         dlam[iu] = 0.0;
+      }
+      if (GQ_IPM_SOFT && s.ns > 0) {
+        // relaxed constraint: slack steps, then its sides' steps with them
+        const int k = soft::soft_smap(box_idx(D, L), nb, nv, s.ns)[c];
+        if (k >= 0) {
+          const soft::SoftSlot q = soft::soft_slot(s, nv, nc, k, c);
+          const bool lo_on = D[L.lo + c] != -INFINITY, hi_on = D[L.hi + c] != INFINITY;
+          const soft::SoftElim e = soft::soft_elim(D, L, s.ns, k, q, lo_on, hi_on, B.lam, B.t, g, rd, rm);
+          soft::soft_recover(e, q, lo_on, hi_on, v, B.lam, B.t, rd, rm, dy, dt, dlam);
+        }
       }
     }
   });
@@ -1104,6 +1167,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
       const StageData L = lay(s);
       const int nc = s.nbu + s.nbx + s.ng;
       for (int c = tid; c < nc; c += blockDim.x) cnt += (D[L.lo + c] != -INFINITY) + (D[L.hi + c] != INFINITY);
+      if (tid == 0) cnt += 2 * s.ns;  // slack bound sides are always active
     });
     atomicAdd(&s_count, cnt);
     __syncthreads();
@@ -1158,18 +1222,26 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
     sweep(C, false, 0, [&](int n, const double* D, const void*) {
       const StageDesc s = sst[n];
       const StageData L = lay(s);
-      const int nc = s.nbu + s.nbx + s.ng;
+      const int nb = s.nbu + s.nbx, nc = nb + s.ng, nv = s.nx + s.nu;
       for (int c = tid; c < nc; c += blockDim.x) {
         const double v = cons_value(s, L, D, c, B.y + s.var);
         const double lo = D[L.lo + c], hi = D[L.hi + c];
         const int il = s.side + c, iu = s.side + nc + c;
+        double sl = 0.0, su = 0.0;  // slacks of a relaxed constraint (Sec. 2.2)
+        if (GQ_IPM_SOFT && s.ns > 0) {
+          const int k = soft::soft_smap(box_idx(D, L), nb, nv, s.ns)[c];
+          if (k >= 0) {
+            sl = B.y[s.var + nv + k];
+            su = B.y[s.var + nv + s.ns + k];
+          }
+        }
         if (lo != -INFINITY) {
           if (warm2) {
             B.lam[il] = fmax(B.lam[il], arg.warm_min);
             B.t[il] = fmax(B.t[il], arg.warm_min);
           } else {
             B.lam[il] = 1.0;
-            B.t[il] = fmax(1.0, v - lo);
+            B.t[il] = fmax(1.0, v + sl - lo);
           }
         } else {
           B.lam[il] = 0.0;
@@ -1181,11 +1253,26 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
             B.t[iu] = fmax(B.t[iu], arg.warm_min);
           } else {
             B.lam[iu] = 1.0;
-            B.t[iu] = fmax(1.0, hi - v);
+            B.t[iu] = fmax(1.0, hi - v + su);
           }
         } else {
           B.lam[iu] = 0.0;
           B.t[iu] = 1.0;
+        }
+      }
+      // slack bound sides s - ls >= 0
+      for (int k = tid; GQ_IPM_SOFT && k < s.ns; k += blockDim.x) {
+        const int jl = s.side + 2 * nc + k, ju = jl + s.ns;
+        if (warm2) {
+          B.lam[jl] = fmax(B.lam[jl], arg.warm_min);
+          B.t[jl] = fmax(B.t[jl], arg.warm_min);
+          B.lam[ju] = fmax(B.lam[ju], arg.warm_min);
+          B.t[ju] = fmax(B.t[ju], arg.warm_min);
+        } else {
+          B.lam[jl] = 1.0;
+          B.t[jl] = fmax(1.0, B.y[s.var + nv + k] - D[L.ls + k]);
+          B.lam[ju] = 1.0;
+          B.t[ju] = fmax(1.0, B.y[s.var + nv + s.ns + k] - D[L.ls + s.ns + k]);
         }
       }
     });
@@ -1370,10 +1457,15 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
 
 }  // namespace
 
+#if GQ_IPM_SOFT
+cudaError_t launch_ipm_soft(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
+                            LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count) {
+#else
 size_t ipm_smem_bytes(const Batch& b, const Shape& sh) { return smem_plan(b, sh).bytes; }
 
 cudaError_t launch_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
                        LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count) {
+#endif
   if (count <= 0) return cudaSuccess;
   const size_t smem = ipm_smem_bytes(b, sh);
   if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;

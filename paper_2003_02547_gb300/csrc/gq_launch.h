@@ -66,5 +66,8 @@ size_t ipm_smem_bytes(const Batch& b, const Shape& sh);
 
 cudaError_t launch_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
                        LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count);
+// the same with the slack elimination of soft constraints compiled in
+cudaError_t launch_ipm_soft(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
+                       LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count);
 
 }  // namespace gq

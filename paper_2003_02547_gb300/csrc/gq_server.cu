@@ -206,11 +206,13 @@ int64_t cache_alloc(gq_server* s, int64_t len, uint64_t key, int64_t nvt, int64_
 struct Plan {
   std::vector<int> dims;
   std::vector<int> slots;
+  std::vector<int> ns;
 };
 
 void plan_dims(const std::vector<Req>& reqs, size_t count, Plan* p) {
   p->dims.clear();
   p->slots.clear();
+  p->ns.clear();
   // stages that read the same source block share one block in the lane
   std::unordered_map<const void*, int> ids;
   ids.reserve(count * 4);
@@ -225,6 +227,7 @@ void plan_dims(const std::vector<Req>& reqs, size_t count, Plan* p) {
       p->dims.push_back(st.nbx);
       p->dims.push_back(st.nbu);
       p->dims.push_back(st.ng);
+      p->ns.push_back(st.ns);
       const void* blk = static_cast<const char*>(src->host_in) + src->L.data + 8 * (int64_t)st.data;
       auto it = ids.find(blk);
       if (it == ids.end()) it = ids.emplace(blk, (int)ids.size()).first;
@@ -247,7 +250,8 @@ int build_batch(gq_server* s, Lane& L, const std::vector<Req>& reqs, size_t coun
   unsigned char* base = L.handle.data();
   unsigned char* mem = base + ((64 - (reinterpret_cast<uintptr_t>(base) % 64)) % 64);
   gq_batch* b = nullptr;
-  int rc = gq_batch_create((int)count, p->dims.data(), p->dims.size(), p->slots.data(), mem, need, &b);
+  int rc = gq_batch_create_soft((int)count, p->dims.data(), p->dims.size(), p->slots.data(), p->ns.data(), mem,
+                                need, &b);
   if (rc) return rc;
   L.b = b;
   f->in_bytes = align256(b->sizes.in_bytes);
@@ -463,7 +467,7 @@ int launch_lane(gq_server* s, Lane& L, std::vector<Req>& reqs) {
       copied[(size_t)slot] = 1;
       const gq::StageDesc& ss = src->st[q.stage0 + n];
       const gq::StageDesc& ds = b->st[b->qp[j].stage0 + n];
-      const gq::StageData lay = gq::stage_data_layout(ss.nx, ss.nu, ss.nx1, ss.nbu + ss.nbx, ss.ng);
+      const gq::StageData lay = gq::stage_data_layout(ss);
       std::memcpy(dst_data + 8 * ds.data, src_data + 8 * ss.data, 8 * (size_t)lay.size);
     }
   }

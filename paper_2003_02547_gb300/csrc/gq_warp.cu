@@ -37,7 +37,7 @@ constexpr double kRegRetry = 1e-10;     // primal regularisation of an FP64 refa
 constexpr double kInexact = 0.1;        // mixed path: direction residual allowed per unit of iterate residual
 
 __device__ __forceinline__ StageData wlay(const StageDesc& s) {
-  return stage_data_layout(s.nx, s.nu, s.nx1, s.nbu + s.nbx, s.ng);
+  return stage_data_layout(s);
 }
 __device__ __forceinline__ int welim(const StageDesc& s, int n) { return n == 0 ? s.nx + s.nu : s.nu; }
 
@@ -1122,8 +1122,7 @@ __global__ void mirror_kernel(const __grid_constant__ Batch B) {
     for (int64_t i = threadIdx.x; i < L.box; i += blockDim.x) dst[i] = (float)src[i];
     const int32_t* si = reinterpret_cast<const int32_t*>(src + L.box);
     int32_t* di = reinterpret_cast<int32_t*>(dst + L.box);
-    const int nint = s.nbu + s.nbx + s.nx + s.nu;
-    for (int i = threadIdx.x; i < nint; i += blockDim.x) di[i] = si[i];
+    for (int i = threadIdx.x; i < L.nint; i += blockDim.x) di[i] = si[i];
   }
 }
 

@@ -85,6 +85,8 @@ SIGNATURES = {
     "gq_ipm_arg_default": (c_int, [ctypes.POINTER(IpmArg), c_int, c_int]),
     "gq_batch_memsize": (c_size_t, [c_int, P_int, c_size_t, P_int]),
     "gq_batch_create": (c_int, [c_int, P_int, c_size_t, P_int, c_void_p, c_size_t, ctypes.POINTER(c_void_p)]),
+    "gq_batch_create_soft": (c_int, [c_int, P_int, c_size_t, P_int, P_int, c_void_p, c_size_t,
+                                     ctypes.POINTER(c_void_p)]),
     "gq_batch_sizes": (c_int, [c_void_p, ctypes.POINTER(Sizes)]),
     "gq_batch_attach": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "gq_set_dynamics": (c_int, [c_void_p, c_int, c_int, P_double, c_int, P_double, c_int, P_double]),
@@ -92,12 +94,16 @@ SIGNATURES = {
                             P_double, P_double]),
     "gq_set_box": (c_int, [c_void_p, c_int, c_int, P_int, P_double, P_double, P_int, P_double, P_double]),
     "gq_set_general": (c_int, [c_void_p, c_int, c_int, P_double, c_int, P_double, c_int, P_double, P_double]),
+    "gq_set_soft": (c_int, [c_void_p, c_int, c_int, P_int, P_double, P_double, P_double, P_double, P_double,
+                            P_double]),
     "gq_set_guess": (c_int, [c_void_p, c_int, P_double, P_double, P_double, P_double]),
     "gq_get_dynamics": (c_int, [c_void_p, c_int, c_int, P_double, c_int, P_double, c_int, P_double]),
     "gq_get_cost": (c_int, [c_void_p, c_int, c_int, P_double, c_int, P_double, c_int, P_double, c_int,
                             P_double, P_double]),
     "gq_get_box": (c_int, [c_void_p, c_int, c_int, P_int, P_double, P_double, P_int, P_double, P_double]),
     "gq_get_general": (c_int, [c_void_p, c_int, c_int, P_double, c_int, P_double, c_int, P_double, P_double]),
+    "gq_get_soft": (c_int, [c_void_p, c_int, c_int, P_int, P_int, P_double, P_double, P_double, P_double, P_double,
+                            P_double]),
     "gq_condense_dims": (c_int, [c_void_p, c_int, c_int, P_int, c_size_t, ctypes.POINTER(c_size_t)]),
     "gq_condense": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
     "gq_expand": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, P_double, P_double, P_double, P_double,
@@ -117,6 +123,7 @@ SIGNATURES = {
     "gq_newton_step": (c_int, [c_void_p, ctypes.POINTER(IpmArg), c_double, c_void_p, c_void_p]),
     "gq_solve_noalloc": (c_int, [c_void_p, ctypes.POINTER(IpmArg), c_void_p, c_void_p, c_void_p]),
     "gq_get_stage_sol": (c_int, [c_void_p, c_int, c_int, P_double, P_double, P_double, P_double, P_double]),
+    "gq_get_stage_slacks": (c_int, [c_void_p, c_int, c_int, P_double, P_double]),
     "gq_get_stats": (c_int, [c_void_p, c_int, ctypes.POINTER(Stats)]),
     "gq_get_statuses": (c_int, [c_void_p, P_int, P_int]),
     "gq_get_sol_offsets": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64)]),
