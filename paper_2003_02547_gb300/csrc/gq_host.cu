@@ -725,7 +725,7 @@ int gq_get_box(gq_batch* b, int qp, int n, int* idxbu, double* lbu, double* ubu,
   StageDesc* s;
   int rc = stage_of(b, qp, n, &s);
   if (rc) return rc;
-  const int nbu = s->nbu, nbx = s->nbx, nb = nbu + nbx;
+  const int nbu = s->nbu, nbx = s->nbx;
   const StageData lay = stage_data_layout(*s);
   const double* D = host_data(b) + s->data;
   const int32_t* I = reinterpret_cast<const int32_t*>(D + lay.box);
