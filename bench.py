@@ -304,13 +304,15 @@ def condensed_run(qps, block: int, dev, precision: int, reps: int = 3):
             "iters_mean": float(np.mean(st["iters"])), "warp_qps": int(sch.warp_qps), "block_qps": int(sch.block_qps)}
 
 
-def batch_run(qps, dev, precision: int, reps: int = 2, mode: int = 0):
+def batch_run(qps, dev, precision: int, reps: int = 2, mode: int = 0, warp_max_nv=None):
     """Device-timed solves of one batch in one call (inputs resident)."""
     import numpy as np
     import torch
     from paper_2003_02547_gb300 import gq
     from paper_2003_02547_gb300.batch import QpBatch
     b = QpBatch(qps, device=dev)
+    if warp_max_nv is not None:
+        b.set_schedule(warp_max_nv, 256)
     arg = gq.default_arg(mode, precision)
     b.upload()
     b.solve(arg)
@@ -562,6 +564,19 @@ def main():
         # without a standing queue
         light = 0.5 * extras["ragged_4096_mixed"]["value"]
         extras["serving_below_capacity"] = serving_run(light, max(1.0, 600.0 / light))
+        # soft constraints (Sec. 2.2): every state box of the mass-spring batch
+        # soft (L2 + L1 penalty); QPs with slacks run in the block kernel, so
+        # the hard batch is timed there too.  Reported, not fatal to the line.
+        try:
+            soft = [W.soften(q, range(1, q.N + 1), "x", Z=10.0, z=1.0, ls=0.0) for q in qps]
+            extras["mass_spring_soft_states"] = {
+                "slack_pairs_per_qp": int(sum(soft[0].ns(n) for n in range(soft[0].N + 1))),
+                "soft_mixed": batch_run(soft, dev, gq.PREC_MIXED),
+                "soft_fp64": batch_run(soft, dev, gq.PREC_FP64),
+                "hard_block_kernel_mixed": batch_run(qps, dev, gq.PREC_MIXED, warp_max_nv=0),
+                "hard_block_kernel_fp64": batch_run(qps, dev, gq.PREC_FP64, warp_max_nv=0)}
+        except Exception as e:
+            extras["mass_spring_soft_states"] = {"error": repr(e)[:300]}
 
     if rank == 0:
         line = {
