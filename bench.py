@@ -6,8 +6,12 @@ Workload (one "step"): the mass-spring chain of Sec. 5.1 with 8 masses
 1e-8 by the mixed-precision IPM (FP32 Riccati factor/solve, FP64 residuals,
 refinement, step length and duality measure) in one kernel launch.
 
-JSON line fields follow the driver contract; see the design doc for the roofline
-arithmetic.  ``--impl reference`` times the CPU oracle instead.
+Prints one JSON line: the metric, its end-to-end counterpart through the C
+ABI with host buffers, the roofline of the timed kernel (algorithmic flops of
+the flop model below over its CUDA-event time, against the flop-mix-weighted
+ALU peak), the sampled SM clocks, the plain per-QP FP64 GPU baseline and the
+CPU oracle on a bounded sample.  ``--impl reference`` times the CPU oracle
+instead.
 """
 from __future__ import annotations
 
@@ -17,6 +21,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -51,7 +56,8 @@ def parse():
 
 
 # ----------------------------------------------------------------------------
-# flop model (algorithmic work per QP)
+# flop model: algorithmic work per QP (stage products, Cholesky, triangular
+# solves and residual mat-vecs of the square-root Riccati IPM)
 # ----------------------------------------------------------------------------
 def qp_flops(qp):
     """(factorisation, one Riccati solve, one residual evaluation) flops."""
@@ -91,7 +97,8 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        out_dir = os.environ.get("GQ_BENCH_OUT", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
