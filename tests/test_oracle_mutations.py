@@ -49,6 +49,40 @@ def _mut_assemble(kind):
     return f
 
 
+def _mut_soft(kind):
+    """Planted mistakes in the slack (soft-constraint) terms of the assembly."""
+    def f(qp):
+        dq = _orig_assemble(qp)
+        act_idx = np.cumsum(dq.active) - 1          # full side -> row of dq.C
+        for n in range(qp.N + 1):
+            m = qp.ns(n)
+            if not m:
+                continue
+            o = dq.var_off[n] + qp.nu[n] + qp.nx[n]
+            c = qp.nbu(n) + qp.nbx(n) + qp.ng(n)
+            s = dq.side_off[n]
+            for k in range(m):
+                jl, ju = o + k, o + m + k
+                if kind == "drop_Z":
+                    dq.H[jl, jl] = dq.H[ju, ju] = 0.0
+                elif kind == "drop_z":
+                    dq.g[jl] = dq.g[ju] = 0.0
+                elif kind == "slack_upper_sign":
+                    full = s + c + int(qp.idxs[n][k])
+                    if dq.active[full]:
+                        dq.C[act_idx[full], ju] = -1.0
+        return dq
+    return f
+
+
+def _soft_pins():
+    import test_oracle_soft as S
+    S.test_scalar_soft_bound_closed_form("lower", 4.0, 0.5)
+    S.test_scalar_soft_bound_closed_form("upper", 10.0, 2.0)
+    for seed in range(6):
+        S.test_soft_brute_force_active_sets(seed)
+
+
 def _mut_step(kind):
     def step(self, rg, rb, rd, rm):
         dq, lam, t = self.dq, self.lam, self.t
@@ -111,6 +145,16 @@ def test_planted_newton_mistake_is_caught(monkeypatch, kind):
     monkeypatch.setattr(O.KktFactor, "step", _mut_step(kind))
     checks = [P.test_reduced_newton_step_equals_full_system, _brute_pins]
     assert _pins_fail(checks) >= 1, kind
+
+
+@pytest.mark.parametrize("kind", ["drop_Z", "drop_z", "slack_upper_sign"])
+def test_planted_slack_mistake_is_caught(monkeypatch, kind):
+    monkeypatch.setattr(O, "assemble", _mut_soft(kind))
+    assert _pins_fail([_soft_pins]) >= 1, kind
+
+
+def test_unmutated_oracle_passes_the_soft_checks():
+    assert _pins_fail([_soft_pins]) == 0
 
 
 def test_unmutated_oracle_passes_the_same_checks():
