@@ -303,7 +303,9 @@ GQ_API int gq_copy_qp(gq_batch* dst, int dst_qp, const gq_batch* src, int src_qp
 /* ---- schedule: which QPs run one per warp, block size of the rest ---- */
 typedef struct gq_schedule {
     int32_t warp_max_nv;   /* QPs whose stages all have nu + nx and nx at most this run
-                              one per warp (0..32; 0: every QP in the block kernel)   */
+                              one per warp (0..32; 0: every QP in the block kernel);
+                              QPs with soft constraints always run in the block
+                              kernel                                                   */
     int32_t block_threads; /* threads per block of the block kernel: 64, 128 or 256    */
     int32_t warp_qps;      /* out: QPs in the warp bucket                             */
     int32_t block_qps;     /* out: QPs in the block bucket                            */
