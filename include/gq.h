@@ -228,7 +228,9 @@ GQ_API int gq_set_box(gq_batch* b, int qp, int n, const int* idxbu, const double
 /* C: ng_n x nx_n, D: ng_n x nu_n, lg, ug: ng_n. */
 GQ_API int gq_set_general(gq_batch* b, int qp, int n, const double* C, int ldc, const double* D, int ldd,
                    const double* lg, const double* ug);
-/* Slack data of stage n (ns_n entries each; nothing to do when ns_n = 0):
+/* Slack data of stage n (ns_n entries each; nothing to do when ns_n = 0;
+ * until it is called, gq_batch_attach leaves slack k relaxing constraint k
+ * at zero cost with zero slack bounds):
  * idxs distinct constraint indices in [0, nc_n), Zl, Zu >= 0 and finite,
  * zl, zu, lls, lus finite.  Errors: GQ_ERR_ARG (NULL pointer, index out of
  * range or repeated), GQ_ERR_DATA (invalid values). */

@@ -468,6 +468,18 @@ int gq_batch_attach(gq_batch* b, void* host_in, void* host_sol, void* dev_in, vo
   if (host_in) {
     char* h = static_cast<char*>(host_in);
     std::memset(h + b->L.data, 0, (size_t)(b->L.in_bytes - b->L.data));
+    // stages with slacks start from a consistent default until gq_set_soft:
+    // slack k relaxes constraint k at zero cost with zero lower bounds
+    for (int64_t i = 0; i < b->n_slots; ++i) {
+      const StageDesc& st = b->st[b->slot_stage[i]];
+      if (st.ns == 0) continue;
+      const StageData lay = stage_data_layout(st);
+      const int nb = st.nbu + st.nbx, nc = nb + st.ng, nv = st.nx + st.nu;
+      int32_t* sidx = reinterpret_cast<int32_t*>(host_data(b) + st.data + lay.box) + nb + nv;
+      int32_t* smap = sidx + st.ns;
+      for (int k = 0; k < st.ns; ++k) sidx[k] = k;
+      for (int c = 0; c < nc; ++c) smap[c] = c < st.ns ? c : -1;
+    }
     std::memcpy(h + b->L.qpdesc, b->qp, (size_t)b->nqp * sizeof(QpDesc));
     std::memcpy(h + b->L.stagedesc, b->st, (size_t)b->n_stages * sizeof(StageDesc));
     std::memcpy(h + b->L.order, b->order, (size_t)b->nqp * sizeof(int32_t));

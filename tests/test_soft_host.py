@@ -99,3 +99,24 @@ def test_condensing_rejects_soft_qps(gqmod):
     b = QpBatch([soft_qp(0)], device=None)
     n = ctypes.c_size_t()
     assert b.lib.gq_condense_dims(b.h, 0, 2, None, 0, ctypes.byref(n)) == gq.GQ_ERR_ARG
+
+
+def test_unset_slack_data_defaults_to_a_consistent_map(gqmod):
+    """Before gq_set_soft, slack k relaxes constraint k (zero cost), so the
+    kernels never meet an inconsistent slack map."""
+    from paper_2003_02547_gb300.batch import QpBatch
+    qp = soft_qp(0)
+    b = QpBatch([qp], device=None, set_data=False)
+    P = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    for n in range(qp.N + 1):
+        m = qp.ns(n)
+        ns = ctypes.c_int()
+        idx = np.full(max(m, 1), -7, dtype=np.int32)
+        vals = [np.full(max(m, 1), 3.0) for _ in range(6)]
+        assert b.lib.gq_get_soft(b.h, 0, n, ctypes.byref(ns), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                 *[P(v) for v in vals]) == 0
+        assert ns.value == m
+        if m:
+            np.testing.assert_array_equal(idx[:m], np.arange(m))
+            for v in vals:
+                assert np.all(v[:m] == 0.0)
