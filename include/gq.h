@@ -6,8 +6,10 @@
  * predictor-corrector interior-point method of Sec. 3.1-3.4 and 4.2.  The
  * Newton system eq. (delta) is reduced to eq. (kkt) by eliminating dt and
  * dlambda (Sec. 3.3) and factorised by the square-root backward Riccati
- * recursion (Sec. 3.3, variant (b)); the whole IPM loop of every QP runs
- * inside CUDA kernels, one thread block per QP.
+ * recursion (Sec. 3.3, variant (b); variant (a), the classical recursion, on
+ * request; the QR array algorithm in modes balance and robust); the whole
+ * IPM loop of every QP runs inside CUDA kernels, one warp or one thread
+ * block per QP.
  *
  * Problem statement (Sec. 2.2).  For stages n = 0..N, y_n = [u_n; x_n]:
  *   min  sum_n 1/2 [u;x;1]' [[R, S, r], [S', Q, q], [r', q', 0]] [u;x;1]
@@ -18,7 +20,9 @@
  * of -INFINITY (lower) or +INFINITY (upper) masks that single side (Sec. 2.1).
  * An initial-state constraint is expressed either by eliminating x_0
  * (nx_0 = 0, x0 folded into b_0, r_0 and the stage-0 general bounds) or, as
- * in the paper, by a box on x_0 with equal bounds.
+ * in the paper, by a box on x_0 with equal bounds.  Any box or general
+ * constraint may be made soft by a slack pair with diagonal L2 and linear
+ * L1 costs (Sec. 2.2; gq_batch_create_soft, gq_set_soft).
  *
  * Sign conventions of the outputs (Lagrangian of Sec. 3.1):
  *   equality rows -B_n u_n - A_n x_n + x_{n+1} = b_n with multiplier pi_{n+1}
