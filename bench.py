@@ -227,6 +227,12 @@ def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: in
         "p99_ms": float(np.percentile(lat, 99)), "admission_wait_share": float(wait.sum() / lat.sum()),
         "converged": int(ok.sum()), "warm_started": int(warm.sum()),
         "not_converged_status": sorted(int(inf.stats.status) for inf in infos if inf.code == 0 and inf.stats.status),
+        # which requests did not converge: arrival index, key, warm request,
+        # horizon and state size of the QP, status, iterations, flags
+        "not_converged": [{"request": i, "key": int(arr[i].key), "warm": bool(arr[i].warm), "N": int(arr[i].qp.N),
+                           "nx": int(max(arr[i].qp.nx)), "status": int(inf.stats.status),
+                           "iters": int(inf.stats.iters), "flags": int(inf.stats.flags)}
+                          for i, inf in enumerate(infos) if inf.code == 0 and inf.stats.status][:20],
         "rejected_or_failed": int(sum(inf.code != 0 for inf in infos)),
         "iters_warm_mean": float(iters[warm].mean()) if warm.any() else None,
         "iters_cold_mean": float(iters[~warm].mean()),
