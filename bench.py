@@ -72,6 +72,21 @@ def qp_flops(qp):
     return f, s, r
 
 
+P32 = 152 * 128 * 2 * 2.07e9   # FP32 FMA lanes x 2 x max SM clock (flop/s)
+P64 = 1.25e12                  # nominal GB300 FP64 rate (flop/s)
+
+
+def alu_roofline(qps, stats, seconds):
+    """Achieved algorithmic flop rates of one batch solve and their fraction
+    of the flop-mix-weighted ALU peak (FP32 lanes for the FP32 work, the FP64
+    rate for the FP64 work)."""
+    f32, f64 = work_split(qps, stats)
+    t_min = f32 / P32 + f64 / P64
+    return {"fp32_tflops": f32 / seconds / 1e12, "fp64_tflops": f64 / seconds / 1e12,
+            "fp32_frac_of_lanes": f32 / seconds / P32, "fp64_frac_of_nominal": f64 / seconds / P64,
+            "frac_of_mix_peak": t_min / seconds if t_min > 0 else None}
+
+
 def work_split(qps, stats):
     """Algorithmic flops of one batch solve split by arithmetic type."""
     f32 = f64 = 0.0
@@ -343,7 +358,8 @@ def batch_run(qps, dev, precision: int, reps: int = 2, mode: int = 0, warp_max_n
     st = b.all_stats()
     out = {"value": len(qps) / (min(ms) * 1e-3), "unit": UNIT, "ms": min(ms), "qps": len(qps),
            "converged": int(np.sum(st["status"] == 0)), "iters_mean": float(np.mean(st["iters"])),
-           "fp64_fallback_qps": int(np.sum(st["flags"] & gq.FLAG_FP64_FALLBACK != 0))}
+           "fp64_fallback_qps": int(np.sum(st["flags"] & gq.FLAG_FP64_FALLBACK != 0)),
+           "alu": alu_roofline(qps, st, min(ms) * 1e-3)}
     if mode == gq.MODE_BALANCE:
         out["array_qr_qps"] = int(np.sum(st["flags"] & gq.FLAG_ARRAY_QR != 0))
     del b
@@ -479,8 +495,6 @@ def main():
 
     # ---------------- roofline of the IPM kernel ----------------
     f32, f64 = work_split(qps, st)
-    P32 = 152 * 128 * 2 * 2.07e9          # FP32 FMA lanes x 2 x max SM clock
-    P64 = 1.25e12                          # nominal GB300 FP64 rate
     t_kernel = mean_ms * 1e-3
     t_min = f32 / P32 + f64 / P64
     achieved = (f32 + f64) / t_kernel
