@@ -447,7 +447,13 @@ def main():
     from paper_2003_02547_gb300.batch import QpBatch
     build.build()
 
-    qps = [W.mass_spring_qp(rank * a.batch + i, M=MASSES, N=HORIZON) for i in range(a.batch)]
+    # one global list of world * batch QPs, split by the LPT rule on the
+    # per-QP cost (every QP of this workload has the same sizes, so one cost
+    # stands for all); each rank solves its shard, no data-path collective
+    from paper_2003_02547_gb300 import shard
+    cost = shard.qp_cost(W.mass_spring_qp(0, M=MASSES, N=HORIZON))
+    mine = shard.lpt_shard([cost] * (world * a.batch), world)[rank]
+    qps = [W.mass_spring_qp(i, M=MASSES, N=HORIZON) for i in mine]
     b = QpBatch(qps, device=dev)
     arg_mixed = gq.default_arg(gq.MODE_SPEED, gq.PREC_MIXED)
     arg_fp64 = gq.default_arg(gq.MODE_SPEED, gq.PREC_FP64)
@@ -483,6 +489,16 @@ def main():
     st = b.all_stats()
     conv = int(np.sum(st["status"] == 0))
     fallback = int(np.sum(st["flags"] & gq.FLAG_FP64_FALLBACK != 0))
+    bad = torch.tensor([a.batch - conv], device=dev, dtype=torch.int64)
+    if world > 1:
+        dist.all_reduce(bad)       # every rank leaves together when any rank failed
+    if int(bad.item()) != 0:
+        # a timed run with an unconverged QP is a failed run, not a number
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world,
+                              "error": f"{int(bad.item())} QPs did not converge in the timed solves",
+                              "statuses": np.bincount(st["status"], minlength=5).tolist()}), flush=True)
+        return 1
     mean_ms = statistics.mean(step_ms)
     tmax = torch.tensor([mean_ms], device=dev, dtype=torch.float64)
     if world > 1:
@@ -518,6 +534,15 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     st_e2e = b.all_stats()
     e2e_ok = int(np.sum(st_e2e["status"] == 0))
+    bad = torch.tensor([a.batch - e2e_ok], device=dev, dtype=torch.int64)
+    if world > 1:
+        dist.all_reduce(bad)
+    if int(bad.item()) != 0:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": None, "unit": UNIT, "n_gpus": world,
+                              "error": f"{int(bad.item())} QPs did not converge in the e2e solves"}),
+                  flush=True)
+        return 1
     e2e_val = a.batch / (statistics.mean(e2e_ms) * 1e-3)
 
     # ---------------- batched FP64 and plain per-QP FP64 GPU baselines ----------------

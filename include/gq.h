@@ -375,6 +375,9 @@ GQ_API int gq_newton_step(gq_batch* b, const gq_ipm_arg* arg, double sigma_mu, v
  *     clearing.  Calls whose GPU work overlaps (other streams, other threads)
  *     race on the array: serialise them. */
 #define GQ_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+/* The size of that array in this build of the library (GQ_NOALLOC_SCRATCH_BYTES
+ * as compiled in), for bindings that cannot read the macro. */
+GQ_API size_t gq_noalloc_scratch_bytes(void);
 GQ_API int gq_solve_noalloc(gq_batch* b, const gq_ipm_arg* arg, void* dev_in, void* dev_sol, void* stream);
 
 /* ---- getters (read host_sol after gq_download + stream sync) ---- */

@@ -849,11 +849,14 @@ static int check_variant(const gq_batch* b, const gq_ipm_arg* a) {
   return GQ_OK;
 }
 
-static int make_kernel_batch(gq_batch* b, Batch* k) {
-  if (!b->dev_in || !b->dev_sol || !b->dev_ws) return fail(GQ_ERR_STATE, "device buffers not attached");
-  char* in = static_cast<char*>(b->dev_in);
-  char* so = static_cast<char*>(b->dev_sol);
-  char* ws = static_cast<char*>(b->dev_ws);
+// Kernel arguments for the batch's layout over the given device buffers (the
+// attached ones for gq_solve; the caller's and the static scratch for
+// gq_solve_noalloc, which leaves the handle untouched).
+static int make_kernel_batch_on(const gq_batch* b, void* dev_in, void* dev_sol, void* dev_ws, Batch* k) {
+  if (!dev_in || !dev_sol || !dev_ws) return fail(GQ_ERR_STATE, "device buffers not attached");
+  char* in = static_cast<char*>(dev_in);
+  char* so = static_cast<char*>(dev_sol);
+  char* ws = static_cast<char*>(dev_ws);
   const Layout& L = b->L;
   k->nqp = b->nqp;
   k->nvmax = b->sizes.nv_max;
@@ -891,6 +894,10 @@ static int make_kernel_batch(gq_batch* b, Batch* k) {
       return fail(GQ_ERR_DIMS, "warp bucket needs %zu bytes of shared memory per block (limit %zu)", smem, kMaxSmem);
   }
   return GQ_OK;
+}
+
+static int make_kernel_batch(const gq_batch* b, Batch* k) {
+  return make_kernel_batch_on(b, b->dev_in, b->dev_sol, b->dev_ws, k);
 }
 
 // both buckets of the batch, in order, on one stream
@@ -1173,6 +1180,8 @@ int noalloc_scratch(void** out) {
 
 }  // namespace
 
+extern "C" size_t gq_noalloc_scratch_bytes(void) { return (size_t)GQ_NOALLOC_SCRATCH_BYTES; }
+
 extern "C" int gq_solve_noalloc(gq_batch* b, const gq_ipm_arg* arg, void* dev_in, void* dev_sol, void* stream) {
   int rc = check_batch(b);
   if (rc) return rc;
@@ -1189,16 +1198,11 @@ extern "C" int gq_solve_noalloc(gq_batch* b, const gq_ipm_arg* arg, void* dev_in
   void* ws = nullptr;
   rc = noalloc_scratch(&ws);
   if (rc) return rc;
-  // the same kernel arguments as gq_solve, with the static scratch as workspace
-  void* saved[3] = {b->dev_in, b->dev_sol, b->dev_ws};
-  b->dev_in = dev_in;
-  b->dev_sol = dev_sol;
-  b->dev_ws = ws;
+  // the same kernel arguments as gq_solve, built over the caller's buffers and
+  // the static scratch; the handle's attached pointers are not touched, so
+  // other threads using the handle meanwhile see no change
   Batch k;
-  rc = make_kernel_batch(b, &k);
-  b->dev_in = saved[0];
-  b->dev_sol = saved[1];
-  b->dev_ws = saved[2];
+  rc = make_kernel_batch_on(b, dev_in, dev_sol, ws, &k);
   if (rc) return rc;
   cudaError_t e = launch_all(b, k, *arg, static_cast<cudaStream_t>(stream), LaunchKind::Solve, 0.0, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "noalloc solve launch");

@@ -19,7 +19,6 @@ FLAG_REGULARIZED = 2
 FLAG_ARRAY_QR = 4
 MODE_SPEED, MODE_BALANCE, MODE_ROBUST = 0, 1, 2
 PREC_FP64, PREC_MIXED = 0, 1
-NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 c_int, c_int64, c_double, c_size_t, c_void_p = (ctypes.c_int, ctypes.c_int64, ctypes.c_double,
                                                 ctypes.c_size_t, ctypes.c_void_p)
@@ -121,6 +120,7 @@ SIGNATURES = {
     "gq_solve": (c_int, [c_void_p, ctypes.POINTER(IpmArg), c_void_p]),
     "gq_residuals": (c_int, [c_void_p, c_void_p]),
     "gq_newton_step": (c_int, [c_void_p, ctypes.POINTER(IpmArg), c_double, c_void_p, c_void_p]),
+    "gq_noalloc_scratch_bytes": (c_size_t, []),
     "gq_solve_noalloc": (c_int, [c_void_p, ctypes.POINTER(IpmArg), c_void_p, c_void_p, c_void_p]),
     "gq_get_stage_sol": (c_int, [c_void_p, c_int, c_int, P_double, P_double, P_double, P_double, P_double]),
     "gq_get_stage_slacks": (c_int, [c_void_p, c_int, c_int, P_double, P_double]),
@@ -180,6 +180,11 @@ def _bind(name):
 # module-level functions with the C names
 for _n in SIGNATURES:
     globals()[_n] = _bind(_n)
+
+
+def noalloc_scratch_bytes() -> int:
+    """Bytes of the static workspace of gq_solve_noalloc, as compiled into the library."""
+    return int(load().gq_noalloc_scratch_bytes())
 
 
 def default_arg(mode: int = MODE_SPEED, precision: int = PREC_FP64, **over) -> IpmArg:

@@ -55,6 +55,13 @@ def test_struct_sizes_match_header(gqmod):
     assert ctypes.sizeof(gqmod.ServerReport) == 15 * 8
 
 
+def test_noalloc_scratch_size_matches_header(gqmod):
+    src = open(os.path.join(ROOT, "include", "gq.h")).read()
+    m = re.search(r"#define GQ_NOALLOC_SCRATCH_BYTES \((\d+)u \* 1024u \* 1024u\)", src)
+    assert m, "GQ_NOALLOC_SCRATCH_BYTES not found in gq.h"
+    assert gqmod.noalloc_scratch_bytes() == int(m.group(1)) * 1024 * 1024
+
+
 def test_arg_defaults(gqmod):
     a = gqmod.default_arg(gqmod.MODE_SPEED, gqmod.PREC_FP64)
     assert a.tol_stat == 1e-8 and a.tau_b == 0.995 and a.ir_steps == 0 and a.reg_prim == 0.0

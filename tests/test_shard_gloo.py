@@ -39,26 +39,32 @@ def _free_port():
 
 def _worker(rank, world, port, out_path):
     import torch.distributed as dist
+    from oracle import ocp_ipm as O
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    qps = [W.small_random_qp(i) for i in range(11)] + [W.ragged_random_qp(i) for i in range(3)]
+    qps = [W.small_random_qp(i) for i in range(9)] + [W.small_random_qp(i, N=5 + i) for i in range(3)]
     costs = [shard.qp_cost(q) for q in qps]
     mine = shard.lpt_shard(costs, world)[rank]
-    # stand-in for the per-GPU solve: a deterministic digest of each QP's data
-    local = {i: (rank, float(sum(np.sum(b) for b in qps[i].b))) for i in mine}
+    # each rank solves its shard (the CPU oracle stands in for the GPU solve)
+    local = {i: (rank, O.solve(qps[i]).y) for i in mine}
     res = shard.gather_results(local, rank, world, dist)
     if rank == 0:
-        with open(out_path, "w") as f:
-            f.write(repr(sorted((k, v[0]) for k, v in res.items())))
+        np.savez(out_path, keys=np.array(sorted(res)), ranks=np.array([res[k][0] for k in sorted(res)]),
+                 **{f"y{k}": res[k][1] for k in res})
     dist.barrier()
     dist.destroy_process_group()
 
 
-def test_gather_over_gloo_world2(tmp_path):
-    out = str(tmp_path / "gathered.txt")
+def test_sharded_solve_gathers_the_unsharded_solutions(tmp_path):
+    from oracle import ocp_ipm as O
+    out = str(tmp_path / "gathered.npz")
     port = _free_port()
     mp.start_processes(_worker, args=(2, port, out), nprocs=2, join=True, start_method="spawn")
-    got = eval(open(out).read())
-    assert [k for k, _ in got] == list(range(14))
-    assert {r for _, r in got} == {0, 1}
+    got = np.load(out)
+    assert got["keys"].tolist() == list(range(12))
+    assert set(got["ranks"].tolist()) == {0, 1}
+    qps = [W.small_random_qp(i) for i in range(9)] + [W.small_random_qp(i, N=5 + i) for i in range(3)]
+    for k, q in enumerate(qps):
+        # the same solve on one process: the gathered solution is identical
+        assert np.array_equal(got[f"y{k}"], O.solve(q).y), k
