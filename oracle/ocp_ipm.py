@@ -111,8 +111,61 @@ def _ns(qp, n: int) -> int:
     return 0 if idxs is None else len(idxs[n])
 
 
-def assemble(qp) -> DenseQp:
-    """Write the stage-wise OCP QP (Sec. 2.2) as one dense generic QP."""
+SPARSE_MIN = 5e7   # ny * (ny + sides) above which the matrices are assembled sparse
+
+
+class _DenseBuilder:
+    def __init__(self, shape):
+        self.a = np.zeros(shape)
+
+    def put(self, r0, c0, blk):
+        blk = np.asarray(blk, dtype=np.float64)
+        self.a[r0:r0 + blk.shape[0], c0:c0 + blk.shape[1]] = blk
+
+    def row(self, r, cols, vals):
+        self.a[r, cols] = vals
+
+    def done(self):
+        return self.a
+
+
+class _SparseBuilder:
+    """The same entries as _DenseBuilder, kept as triplets (a block's zeros
+    included), for QPs whose dense matrices would not fit in memory."""
+
+    def __init__(self, shape):
+        self.shape = shape
+        self.r, self.c, self.v = [], [], []
+
+    def put(self, r0, c0, blk):
+        blk = np.asarray(blk, dtype=np.float64)
+        h, w = blk.shape
+        rr, cc = np.meshgrid(np.arange(r0, r0 + h), np.arange(c0, c0 + w), indexing="ij")
+        self.r.append(rr.ravel())
+        self.c.append(cc.ravel())
+        self.v.append(blk.ravel())
+
+    def row(self, r, cols, vals):
+        cols = np.atleast_1d(np.asarray(cols))
+        self.r.append(np.full(cols.size, r))
+        self.c.append(cols)
+        self.v.append(np.atleast_1d(np.asarray(vals, dtype=np.float64)))
+
+    def done(self):
+        if not self.r:
+            return scipy.sparse.csr_matrix(self.shape)
+        r, c, v = np.concatenate(self.r), np.concatenate(self.c), np.concatenate(self.v)
+        # later entries overwrite earlier ones at the same position (as in the dense builder)
+        key = r.astype(np.int64) * self.shape[1] + c
+        _, last = np.unique(key[::-1], return_index=True)
+        keep = key.size - 1 - last
+        return scipy.sparse.csr_matrix((v[keep], (r[keep], c[keep])), shape=self.shape)
+
+
+def assemble(qp, sparse: Optional[bool] = None) -> DenseQp:
+    """Write the stage-wise OCP QP (Sec. 2.2) as one generic QP; H, A and C
+    are dense arrays, or scipy.sparse CSR matrices with the same entries for
+    QPs too large for dense storage (``sparse=None`` decides by size)."""
     N = qp.N
     ns = [_ns(qp, n) for n in range(N + 1)]
     nv = [qp.nx[n] + qp.nu[n] + 2 * ns[n] for n in range(N + 1)]
@@ -124,71 +177,71 @@ def assemble(qp) -> DenseQp:
     nc = [qp.nbu(n) + qp.nbx(n) + qp.ng(n) for n in range(N + 1)]
     side_off = np.concatenate([[0], np.cumsum([2 * nc[n] + 2 * ns[n] for n in range(N + 1)])]).astype(int)
     nside = int(side_off[-1])
+    if sparse is None:
+        sparse = float(ny) * float(ny + nside) > SPARSE_MIN
+    Builder = _SparseBuilder if sparse else _DenseBuilder
 
-    H = np.zeros((ny, ny))
+    Hb = Builder((ny, ny))
     g = np.zeros(ny)
     for n in range(N + 1):
         o, nu, nx = var_off[n], qp.nu[n], qp.nx[n]
-        H[o:o + nu, o:o + nu] = qp.R[n]
-        H[o:o + nu, o + nu:o + nu + nx] = qp.S[n]
-        H[o + nu:o + nu + nx, o:o + nu] = qp.S[n].T
-        H[o + nu:o + nu + nx, o + nu:o + nu + nx] = qp.Q[n]
+        Hb.put(o, o, qp.R[n])
+        Hb.put(o, o + nu, qp.S[n])
+        Hb.put(o + nu, o, qp.S[n].T)
+        Hb.put(o + nu, o + nu, qp.Q[n])
         g[o:o + nu] = qp.r[n]
         g[o + nu:o + nu + nx] = qp.q[n]
         for k in range(ns[n]):
             # slack costs 1/2 Z s^2 + z s, s^l block then s^u block
             jl, ju = o + nu + nx + k, o + nu + nx + ns[n] + k
-            H[jl, jl] = qp.Zl[n][k]
-            H[ju, ju] = qp.Zu[n][k]
+            Hb.row(jl, jl, qp.Zl[n][k])
+            Hb.row(ju, ju, qp.Zu[n][k])
             g[jl] = qp.zl[n][k]
             g[ju] = qp.zu[n][k]
+    H = Hb.done()
 
-    A = np.zeros((neq, ny))
+    Ab = Builder((neq, ny))
     b = np.zeros(neq)
     for n in range(N):
-        rows = slice(eq_off[n], eq_off[n + 1])
+        r0 = eq_off[n]
         o, nu, nx = var_off[n], qp.nu[n], qp.nx[n]
-        A[rows, o:o + nu] = -qp.B[n]
-        A[rows, o + nu:o + nu + nx] = -qp.A[n]
+        Ab.put(r0, o, -qp.B[n])
+        Ab.put(r0, o + nu, -qp.A[n])
         o1, nu1, nx1 = var_off[n + 1], qp.nu[n + 1], qp.nx[n + 1]
-        A[rows, o1 + nu1:o1 + nu1 + nx1] = np.eye(nx1)
-        b[rows] = qp.b[n]
+        Ab.put(r0, o1 + nu1, np.eye(nx1))
+        b[eq_off[n]:eq_off[n + 1]] = qp.b[n]
+    A = Ab.done()
 
-    Crow = np.zeros((nside, ny))
+    Cb = Builder((nside, ny))
     dfull = np.zeros(nside)
     active = np.zeros(nside, dtype=bool)
     for n in range(N + 1):
         o, nu = var_off[n], qp.nu[n]
-        rows = []
+        rows = []   # (columns, values) of each constraint row c(y)
         lo = []
         hi = []
         for k, i in enumerate(qp.idxbu[n]):
-            r = np.zeros(ny)
-            r[o + int(i)] = 1.0
-            rows.append(r)
+            rows.append((np.array([o + int(i)]), np.array([1.0])))
             lo.append(qp.lbu[n][k])
             hi.append(qp.ubu[n][k])
         for k, i in enumerate(qp.idxbx[n]):
-            r = np.zeros(ny)
-            r[o + nu + int(i)] = 1.0
-            rows.append(r)
+            rows.append((np.array([o + nu + int(i)]), np.array([1.0])))
             lo.append(qp.lbx[n][k])
             hi.append(qp.ubx[n][k])
+        cols_g = np.arange(o, o + nu + qp.nx[n])
         for k in range(qp.ng(n)):
-            r = np.zeros(ny)
-            r[o:o + nu] = qp.D[n][k]
-            r[o + nu:o + nu + qp.nx[n]] = qp.C[n][k]
-            rows.append(r)
+            rows.append((cols_g, np.concatenate([qp.D[n][k], qp.C[n][k]])))
             lo.append(qp.lg[n][k])
             hi.append(qp.ug[n][k])
         c = len(rows)
         s = side_off[n]
         for k in range(c):
             # lower side: c(y) - lo >= 0 ; upper side: -c(y) + hi >= 0
-            Crow[s + k] = rows[k]
+            cols, vals = rows[k]
+            Cb.row(s + k, cols, vals)
             dfull[s + k] = lo[k]
             active[s + k] = np.isfinite(lo[k])
-            Crow[s + c + k] = -rows[k]
+            Cb.row(s + c + k, cols, -vals)
             dfull[s + c + k] = -hi[k]
             active[s + c + k] = np.isfinite(hi[k])
         m = ns[n]
@@ -197,15 +250,17 @@ def assemble(qp) -> DenseQp:
             # lower bound of its own on each
             ci = int(qp.idxs[n][k])
             jl, ju = o + nu + qp.nx[n] + k, o + nu + qp.nx[n] + m + k
-            Crow[s + ci, jl] = 1.0
-            Crow[s + c + ci, ju] = 1.0
-            Crow[s + 2 * c + k, jl] = 1.0
+            Cb.row(s + ci, jl, 1.0)
+            Cb.row(s + c + ci, ju, 1.0)
+            Cb.row(s + 2 * c + k, jl, 1.0)
             dfull[s + 2 * c + k] = qp.lls[n][k]
             active[s + 2 * c + k] = True
-            Crow[s + 2 * c + m + k, ju] = 1.0
+            Cb.row(s + 2 * c + m + k, ju, 1.0)
             dfull[s + 2 * c + m + k] = qp.lus[n][k]
             active[s + 2 * c + m + k] = True
-    return DenseQp(H=H, g=g, A=A, b=b, C=Crow[active], d=dfull[active], active=active,
+    Crow = Cb.done()
+    C = Crow[np.flatnonzero(active)] if sparse else Crow[active]
+    return DenseQp(H=H, g=g, A=A, b=b, C=C, d=dfull[active], active=active,
                    ny=ny, neq=neq, nside=nside, var_off=list(var_off),
                    eq_off=list(eq_off), side_off=list(side_off))
 
@@ -229,10 +284,15 @@ class KktFactor:
         self.lam = lam
         self.t = t
         W = lam / t
-        Ht = dq.H + dq.C.T @ (W[:, None] * dq.C)
         n = dq.ny + dq.neq
         self.n = n
-        dense = (n <= DENSE_MAX) if force_dense is None else force_dense
+        if scipy.sparse.issparse(dq.H):
+            # sparse assembly (large QPs): the same Ht with sparse products
+            Ht = dq.H + dq.C.T @ scipy.sparse.diags(W) @ dq.C
+            dense = False
+        else:
+            Ht = dq.H + dq.C.T @ (W[:, None] * dq.C)
+            dense = (n <= DENSE_MAX) if force_dense is None else force_dense
         self.dense = dense
         if dense:
             K = np.zeros((n, n))

@@ -83,8 +83,8 @@ def test_large_stage_reduced_horizon(env):
 def test_large_stage_full_batch(env, precision):
     """256 QPs with N = 100, nx = 128, nu = 64 in one solve call: every QP
     converged, and the KKT residuals of a sample recomputed on the CPU meet
-    the exit rule (the oracle's sparse solve at this size takes minutes per
-    QP, so the oracle comparison runs at N = 6 above)."""
+    the exit rule (two of these QPs are compared with the oracle's sparse
+    solve at the full horizon in test_gpu_optimum.py)."""
     qps = W.large_stage_batch(256)
     b = GP.solve_gpu(env, qps, precision=precision)
     st = b.all_stats()

@@ -394,6 +394,25 @@ def test_dense_and_sparse_solves_agree():
     np.testing.assert_allclose(a.pi, b.pi, atol=1e-9)
 
 
+def test_sparse_assembly_has_the_dense_entries():
+    """Large QPs are assembled as sparse matrices: the same entries as the
+    dense assembly (stage-varying sizes, S != 0, general rows, masked sides,
+    soft constraints), and the same converged point through the sparse LU."""
+    qps = [random_lq(77, N=5, boxes=True, ng=2, tight=0.8), W.ragged_random_qp(16),
+           W.soften(W.small_random_qp(2, x0_scale=2.0), range(0, 10), "u", Z=0.5, z=1.0, ls=-0.05)]
+    for qp in qps:
+        d, s = O.assemble(qp, sparse=False), O.assemble(qp, sparse=True)
+        for name in ("H", "A", "C"):
+            assert np.array_equal(getattr(d, name), getattr(s, name).toarray()), name
+        for name in ("g", "b", "d", "active"):
+            assert np.array_equal(getattr(d, name), getattr(s, name)), name
+        a = O.solve(qp, O.IpmArg(force_dense=False), dq=d)
+        b = O.solve(qp, dq=s)
+        assert a.status == b.status == O.CONVERGED
+        np.testing.assert_allclose(b.y, a.y, atol=1e-10)
+        assert abs(O.duality_gap(s, b.y, b.pi, b.lam[s.active])) <= 1e-7
+
+
 def test_equal_bound_initial_state_variant():
     """x_0 kept as a variable fixed by lb = ub box bounds (the paper's
     formulation, Sec. 2.2) gives the same solution as eliminating x_0."""
