@@ -56,7 +56,8 @@ struct WCtx {
   const Batch* B;
   const StageDesc* st;
   int N, nact, nside, side0, v0, v1, e0, e1, lane;
-  unsigned char* ring[2];
+  unsigned char* ring0;  // two consecutive ring slots of `slot` bytes (no indexed
+  uint32_t slot;         // array: keeps the context in registers)
   uint64_t* bar;
   uint32_t parity;
   uint32_t fac_off;
@@ -92,8 +93,8 @@ __device__ __forceinline__ void wissue(WCtx& C, int n, int b, const unsigned cha
     const uint32_t fbytes = felem ? (uint32_t)(fac_block_elems(s.nx + s.nu) * felem) : 0u;
     fence_async_shared();
     mbar_arrive_expect_tx(&C.bar[b], dbytes + fbytes);
-    bulk_g2s(C.ring[b], dbase + s.data * delem, dbytes, &C.bar[b]);
-    if (fbytes) bulk_g2s(C.ring[b] + C.fac_off, fbase + s.fac * 8, fbytes, &C.bar[b]);
+    bulk_g2s((C.ring0 + b * C.slot), dbase + s.data * delem, dbytes, &C.bar[b]);
+    if (fbytes) bulk_g2s(C.ring0 + b * C.slot + C.fac_off, fbase + s.fac * 8, fbytes, &C.bar[b]);
   }
 }
 
@@ -111,7 +112,7 @@ __device__ void wsweep(WCtx& C, bool backward, const void* dbase, int delem, con
     const bool ok = C.ok && mbar_wait(&C.bar[b], (C.parity >> b) & 1u);
     C.parity ^= 1u << b;
     C.ok = C.ok && ok;
-    f(n, static_cast<const void*>(C.ring[b]), static_cast<const void*>(C.ring[b] + C.fac_off));
+    f(n, static_cast<const void*>((C.ring0 + b * C.slot)), static_cast<const void*>(C.ring0 + b * C.slot + C.fac_off));
     __syncwarp();
   }
 }
@@ -787,7 +788,10 @@ __device__ double wmu_after(const WCtx& C, double alpha, const double* dlam, con
 constexpr int kStatusResumeFp64 = 100;
 
 template <typename T>
-__global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Batch B, const WarpPlan P,
+// one warp per block; the register limit (in place of launch bounds, which cap
+// a 32-thread kernel's registers low enough to spill) keeps the whole solver
+// context in registers, and 12 blocks still fit an SM
+__global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B, const WarpPlan P,
                                                       const __grid_constant__ gq_ipm_arg arg, int kind,
                                                       double sigma_mu, const DirOut out, const int32_t* order) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -818,8 +822,8 @@ __global__ void __launch_bounds__(32) warp_ipm_kernel(const __grid_constant__ Ba
   C.e0 = qd.eq0;
   C.e1 = qd.eq0 + qd.neqt;
   C.lane = lane;
-  C.ring[0] = smem + P.ring0;
-  C.ring[1] = smem + P.ring1;
+  C.ring0 = smem + P.ring0;
+  C.slot = (uint32_t)(P.ring1 - P.ring0);
   C.bar = bars;
   C.parity = 0;
   C.fac_off = (uint32_t)P.fac_off;
