@@ -236,42 +236,93 @@ int gq_condense(gq_batch* src, int src_qp, int block, gq_batch* dst, int dst_qp)
     const StageDims dd = dims_of(dst, dst_qp, k);
     if (dd.nx != nxp || dd.nu != nup || dd.nx1 != nx1p)
       return set_error(GQ_ERR_DIMS, "destination stage %d has other sizes than the condensed block", k);
-    // cost: H' = sum T' H T, g' = sum T' (H [0; c] + g)
-    Mat H((size_t)nvp * nvp, 0.0);
-    std::vector<double> g(nvp, 0.0), tr, hc;
-    for (int j = 0; j < mlen; ++j) {
-      const StageData& s = st[j];
-      const int nu = s.d.nu, nx = s.d.nx, nv = nu + nx;
-      std::vector<Mat> Trows(nv);
-      for (int r = 0; r < nv; ++r) t_row(m, j, nu, r, &Trows[r]);
-      // stage Hessian [[R, S], [S', Q]] and gradient [r; q]
-      auto Hs = [&](int a, int c2) -> double {
-        if (a < nu && c2 < nu) return s.R[(size_t)a * nu + c2];
-        if (a < nu) return s.S[(size_t)a * nx + (c2 - nu)];
-        if (c2 < nu) return s.S[(size_t)c2 * nx + (a - nu)];
-        return s.Q[(size_t)(a - nu) * nx + (c2 - nu)];
-      };
-      // w = H [0; c_j] + g
-      std::vector<double> w(nv, 0.0);
-      for (int a = 0; a < nv; ++a) {
-        double v = a < nu ? s.r[a] : s.q[a - nu];
-        for (int c2 = nu; c2 < nv; ++c2) v += Hs(a, c2) * m.c[j][c2 - nu];
-        w[a] = v;
-      }
-      for (int a = 0; a < nv; ++a) {
-        for (int c2 = 0; c2 < nv; ++c2) {
-          const double h = Hs(a, c2);
-          if (h == 0.0) continue;
-          const Mat& ta = Trows[a];
-          const Mat& tc = Trows[c2];
-          for (int p = 0; p < nvp; ++p) {
-            if (ta[p] == 0.0) continue;
-            const double f = ta[p] * h;
-            for (int q2 = 0; q2 < nvp; ++q2) H[(size_t)p * nvp + q2] += f * tc[q2];
-          }
+    // cost: the backward recursion of Sec. 3.5 (condensing analogous to the
+    // classical Riccati recursion), quadratic in the block length and cubic
+    // in the state size.  The cost of stages j..m-1 as a function of
+    // v_j = [u_j; u_{j+1..}; x_j] is 1/2 v_j' W_j v_j + w_j' v_j; W_m = 0 on x_m,
+    // and with x_{j+1} = A x_j + B u_j + b and W_{j+1} = [[Wuu, Wux], [Wxu, Wxx]]:
+    //   W_j = [[R + B'Wxx B,  B'Wxu,  S + B'Wxx A],
+    //          [Wux' B,       Wuu,    Wux A      ],
+    //          [.,            .,      Q + A'Wxx A]]   (symmetric)
+    //   w_j = [r + B'(Wxx b + wx); wu + Wux b; q + A'(Wxx b + wx)].
+    // W_0 is the condensed Hessian over [u'; x'] and w_0 its gradient.
+    Mat H;
+    std::vector<double> g;
+    {
+      int U = 0, X = st.back().d.nx1;  // sizes of the tail's inputs and of its state
+      Mat W((size_t)X * X, 0.0);       // (U + X) x (U + X), row-major
+      std::vector<double> w((size_t)X, 0.0);
+      for (int j = mlen - 1; j >= 0; --j) {
+        const StageData& s = st[j];
+        const int nu = s.d.nu, nx = s.d.nx, nx1 = s.d.nx1, n1 = U + X;
+        auto Wv = [&](int a, int c2) { return W[(size_t)a * n1 + c2]; };
+        // P = Wxx (X x X), K = Wux (U x X), e = Wxx b + wx
+        std::vector<double> e((size_t)nx1, 0.0);
+        for (int i = 0; i < nx1; ++i) {
+          double v = w[(size_t)U + i];
+          for (int k = 0; k < nx1; ++k) v += Wv(U + i, U + k) * s.b[k];
+          e[i] = v;
         }
-        for (int p = 0; p < nvp; ++p) g[p] += Trows[a][p] * w[a];
+        // PB = Wxx [B A] (X x (nu + nx)), KB = Wux [B A] (U x (nu + nx))
+        const int nvj = nu + nx;
+        auto BA = [&](int k, int c2) { return c2 < nu ? s.B[(size_t)k * nu + c2] : s.A[(size_t)k * nx + (c2 - nu)]; };
+        Mat PB((size_t)nx1 * nvj, 0.0), KB((size_t)U * nvj, 0.0);
+        for (int i = 0; i < nx1; ++i)
+          for (int k = 0; k < nx1; ++k) {
+            const double p = Wv(U + i, U + k);
+            if (p == 0.0) continue;
+            for (int c2 = 0; c2 < nvj; ++c2) PB[(size_t)i * nvj + c2] += p * BA(k, c2);
+          }
+        for (int i = 0; i < U; ++i)
+          for (int k = 0; k < nx1; ++k) {
+            const double p = Wv(i, U + k);
+            if (p == 0.0) continue;
+            for (int c2 = 0; c2 < nvj; ++c2) KB[(size_t)i * nvj + c2] += p * BA(k, c2);
+          }
+        // new ordering [u_j (nu); u_{j+1..} (U); x_j (nx)]
+        const int U2 = nu + U, n2 = U2 + nx;
+        Mat W2((size_t)n2 * n2, 0.0);
+        std::vector<double> w2((size_t)n2, 0.0);
+        auto idx = [&](int c2) { return c2 < nu ? c2 : U2 + (c2 - nu); };  // [u_j; x_j] -> position
+        // [B A]' Wxx [B A] + stage Hessian
+        for (int a2 = 0; a2 < nvj; ++a2)
+          for (int c2 = 0; c2 < nvj; ++c2) {
+            double v = 0.0;
+            for (int k = 0; k < nx1; ++k) v += BA(k, a2) * PB[(size_t)k * nvj + c2];
+            double h;
+            if (a2 < nu && c2 < nu) h = s.R[(size_t)a2 * nu + c2];
+            else if (a2 < nu) h = s.S[(size_t)a2 * nx + (c2 - nu)];
+            else if (c2 < nu) h = s.S[(size_t)c2 * nx + (a2 - nu)];
+            else h = s.Q[(size_t)(a2 - nu) * nx + (c2 - nu)];
+            W2[(size_t)idx(a2) * n2 + idx(c2)] = h + v;
+          }
+        // Wux [B A] couples the later inputs with [u_j; x_j]
+        for (int i = 0; i < U; ++i)
+          for (int c2 = 0; c2 < nvj; ++c2) {
+            const double v = KB[(size_t)i * nvj + c2];
+            W2[(size_t)(nu + i) * n2 + idx(c2)] = v;
+            W2[(size_t)idx(c2) * n2 + nu + i] = v;
+          }
+        for (int i = 0; i < U; ++i)
+          for (int k = 0; k < U; ++k) W2[(size_t)(nu + i) * n2 + nu + k] = Wv(i, k);
+        // gradient
+        for (int c2 = 0; c2 < nvj; ++c2) {
+          double v = c2 < nu ? s.r[c2] : s.q[c2 - nu];
+          for (int k = 0; k < nx1; ++k) v += BA(k, c2) * e[k];
+          w2[idx(c2)] = v;
+        }
+        for (int i = 0; i < U; ++i) {
+          double v = w[i];
+          for (int k = 0; k < nx1; ++k) v += Wv(i, U + k) * s.b[k];
+          w2[(size_t)nu + i] = v;
+        }
+        W.swap(W2);
+        w.swap(w2);
+        U = U2;
+        X = nx;
       }
+      H.swap(W);
+      g.swap(w);
     }
     for (int p = 0; p < nvp; ++p)
       for (int q2 = 0; q2 < p; ++q2) {

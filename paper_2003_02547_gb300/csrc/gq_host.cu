@@ -418,6 +418,8 @@ int gq_batch_create_soft(int nqp, const int* dims, size_t dims_len, const int* s
   o = align_up(o + data * 4, 256);
   L.matg = o;
   o = align_up(o + matg_elems * 8, 256);
+  L.queue = o;
+  o = align_up(o + kQueueSlots * 4, 256);
   L.ws_bytes = o;
 
   gq_sizes& z = b->sizes;
@@ -881,6 +883,7 @@ static int make_kernel_batch_on(const gq_batch* b, void* dev_in, void* dev_sol, 
   for (int i = 0; i < 16; ++i) *w[i] = reinterpret_cast<double*>(ws + off[i]);
   k->fac = ws + L.fac;
   k->matg = reinterpret_cast<double*>(ws + L.matg);
+  k->queue = reinterpret_cast<int32_t*>(ws + L.queue);
   if (b->nwarp < b->nqp) {
     const size_t smem = ipm_smem_bytes(*k, b->shape_b);
     if (smem > kMaxSmem)

@@ -43,6 +43,7 @@
 #include "gq_launch.h"
 #include "gq_mma.h"
 #include "gq_soft.h"
+#include "gq_tc.h"
 
 // Soft constraints (Sec. 2.2): the slack elimination is compiled in only when
 // GQ_IPM_SOFT is 1 (gq_ipm_soft.cu builds this file that way and exports
@@ -71,6 +72,14 @@ __host__ __device__ SmemPlan smem_plan(const Batch& b, const Shape& sh) {
   p.mat = sh.mat_global ? 0 : take((size_t)block_mat_elems(sh) * sizeof(double), 16);
   p.panel = take((size_t)(sh.nvmax > 0 ? sh.nvmax : 1) * kBlockPanel * sizeof(double), 16);
   p.stages = take((size_t)sh.nst_max * sizeof(StageDesc), 16);
+  // tensor-core operand tiles (TF32 high and low parts of A and of B), the
+  // MMA-completion mbarrier and the TMEM address
+  if (tc_shape(sh)) {
+    p.tc = take(4 * tc_tile_bytes(), 1024);
+    p.tcbar = take(16, 16);
+  } else {
+    p.tc = p.tcbar = 0;
+  }
   // ring: two buffers of (data block + FP64-sized factor block)
   p.ring_fac = (size_t)((sh.data_max * 8 + 127) / 128 * 128);
   const size_t slot = p.ring_fac + (size_t)fac_block_elems(sh.nvmax) * sizeof(double);
@@ -149,6 +158,13 @@ struct Ctx {
   bool classical;  // classical Riccati: explicit P_{n+1} in place of L_{n+1}
   bool array_qr;   // robust mode: chol(Ht + M M') by QR of [chol(Ht)'; M']
   Ring ring;
+  // tensor-core stage products (FP32 factor of large stages)
+  bool tc;            // TMEM allocated and the shape qualifies
+  uint32_t taddr;     // TMEM base address (kTcCols columns)
+  uint64_t* tcbar;    // MMA-completion mbarrier
+  uint32_t tcpar;     // its next phase parity
+  float* tcA;         // A tile: high part, then the low part tc_tile_bytes() later
+  float* tcB;         // B tile: high part, then the low part
 };
 
 // Sum of f(i), i in [0, count), in an order fixed by `count` alone: 32-term
@@ -242,26 +258,16 @@ __device__ __forceinline__ Tf* fac_global(const Batch& B, const StageDesc& s) {
   return reinterpret_cast<Tf*>(static_cast<double*>(B.fac) + s.fac);
 }
 
-// values of the general rows [D C] y of stage s (FP64, row-parallel dot
-// products with short dependent chains) into gv[ng]; block-wide, ends with a
-// barrier when ng > 0.  Every thread of the block must call it.
-__device__ __forceinline__ void general_values(const StageDesc& s, const StageData& L, const double* D,
-                                               const double* y, double* gv) {
-  const int nv = s.nx + s.nu;
-  if (s.ng > 0) {  // uniform across the block
-    rows_dot<double>(
-        s.ng, [&](int) { return 0; }, [&](int) { return nv; },
-        [&](int g, int j) { return D[L.DC + (int64_t)g * nv + j] * y[j]; }, [&](int g, double v) { gv[g] = v; });
-    __syncthreads();
-  }
-}
-
-// value of constraint c of stage s at y, general rows from general_values
+// value of constraint c of stage s at the stage vector y (length nv)
 __device__ __forceinline__ double cons_value(const StageDesc& s, const StageData& L, const double* D, int c,
-                                             const double* y, const double* gv) {
+                                                    const double* y) {
   const int nb = s.nbu + s.nbx;
   if (c < nb) return y[box_idx(D, L)[c]];
-  return gv[c - nb];
+  const int nv = s.nx + s.nu;
+  const double* row = D + L.DC + (int64_t)(c - nb) * nv;
+  double v = 0.0;
+  for (int j = 0; j < nv; ++j) v = fma(row[j], y[j], v);
+  return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -340,18 +346,17 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
   // r_g rows: [RSQ row | [B A]' row] . [y_n | pi_{n+1}], then the rest
   {
     const double* pn1 = pi + s.eq;
-    const int kdyn = n < C.N ? nv + nx1 : nv;  // then the ng general-row terms
+    const int kend = n < C.N ? nv + nx1 : nv;
     rows_dot<double>(
-        nv, [&](int) { return 0; }, [&](int) { return kdyn + s.ng; },
+        nv, [&](int) { return 0; }, [&](int) { return kend; },
         [&](int i, int k) {
-          if (k < nv) return D[L.RSQ + (int64_t)i * L.ldr + k] * yn[k];
-          if (k < kdyn) return D[L.BAt + (int64_t)i * L.ldb + (k - nv)] * pn1[k - nv];
-          const int g = k - kdyn;
-          return -D[L.DC + (int64_t)g * nv + i] * (lm[nb + g] - lm[nc + nb + g]);
+          return k < nv ? D[L.RSQ + (int64_t)i * L.ldr + k] * yn[k] : D[L.BAt + (int64_t)i * L.ldb + (k - nv)] * pn1[k - nv];
         },
         [&](int i, double v) {
           double acc = (lin ? add_g[s.var + i] : D[L.rq + i]) + v;
           if (n > 0 && i >= s.nu) acc -= pi[C.st[n - 1].eq + (i - s.nu)];
+          for (int g = 0; g < s.ng; ++g)
+            acc = fma(-D[L.DC + (int64_t)g * nv + i], lm[nb + g] - lm[nc + nb + g], acc);
           if (nb > 0) {
             const int c = bmap[i];
             if (c >= 0) acc -= lm[c] - lm[nc + c];
@@ -372,10 +377,8 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
         });
   }
   if (rd != nullptr) {
-    double* gv = C.vbuf + 6 * C.vmax;
-    general_values(s, L, D, yn, gv);
     for (int c = tid; c < nc; c += NT) {
-      const double v = cons_value(s, L, D, c, yn, gv);
+      const double v = cons_value(s, L, D, c, yn);
       const double lo = D[L.lo + c], hi = D[L.hi + c];
       const int il = s.side + c, iu = s.side + nc + c;
       double a = 0.0, b = 0.0;
@@ -449,8 +452,131 @@ __device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
   J = t - i * (i + 1) / 2;
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core stage products of the FP32 factor (tcgen05, Blackwell):
+//   M = [B A]' L_{n+1}          (nv x nx1, stored transposed as M')
+//   Phi = RSQ + M M' + diag     (lower triangle)
+// Each FP32 operand is split into a TF32 high part and a TF32 remainder and
+// three kind::tf32 MMAs (lo*hi + hi*lo + hi*hi) accumulate in FP32 in TMEM,
+// which keeps the products at FP32 accuracy.  Operand chunks of kTcK columns
+// are staged in shared memory by all threads in the K-major layout of gq_tc.h;
+// one thread issues the MMAs of a chunk and commits them to an mbarrier that
+// every thread waits on (bounded) before the next chunk is staged.  Rows are
+// padded to 128 (one M = 128 tile) or 256 (two tiles); zero padding.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tc_put(float* tile, int r, int k, float v) {
+  const uint32_t o = tc::kmajor_off(r, k, kTcK) >> 2;
+  const float hi = tc::tf32_round(v);
+  tile[o] = hi;
+  tile[o + (tc_tile_bytes() >> 2)] = tc::tf32_round(v - hi);
+}
+
+// one chunk: D[tile t] (+)= A[rows t*128..] B^T for every tile t in [t0, t1),
+// B rows starting at brow, N columns; accumulate after the first chunk
+__device__ __forceinline__ void tc_chunk_mma(Ctx& C, int t0, int t1, int brow, int N, uint32_t dcol, bool acc) {
+  if (threadIdx.x == 0) {
+    tc::fence_after();
+    const uint32_t sbo = (kTcK / 4) * 128, lo = (uint32_t)tc_tile_bytes();
+    const uint32_t a0 = tc::s32(C.tcA), b0 = tc::s32(C.tcB) + (uint32_t)(brow / 8) * sbo;
+    const uint32_t id = tc::idesc_tf32(128, N);
+    for (int t = t0; t < t1; ++t) {
+      const uint32_t d = C.taddr + dcol + (uint32_t)((t - t0) * N);
+      const uint32_t at = a0 + (uint32_t)(t * 16) * sbo;
+#pragma unroll
+      for (int s8 = 0; s8 < kTcK; s8 += 8) {
+        const uint32_t ko = (uint32_t)s8 * 32;  // two core matrices along K per step
+        const uint64_t ah = tc::sdesc(at + ko, 128, sbo), al = tc::sdesc(at + lo + ko, 128, sbo);
+        const uint64_t bh = tc::sdesc(b0 + ko, 128, sbo), bl = tc::sdesc(b0 + lo + ko, 128, sbo);
+        tc::mma_tf32(d, al, bh, id, acc || s8 > 0);
+        tc::mma_tf32(d, ah, bl, id, true);
+        tc::mma_tf32(d, ah, bh, id, true);
+      }
+    }
+    tc::commit(C.tcbar);
+  }
+  // every thread waits for the chunk's MMAs (bounded; a lost completion
+  // makes the QP time out like a lost bulk copy)
+  const bool ok = C.ring.ok && mbar_wait(C.tcbar, C.tcpar);
+  C.tcpar ^= 1u;
+  C.ring.ok = C.ring.ok && ok;
+  tc::fence_after();
+}
+
+__device__ void tc_products(Ctx& C, int n, const double* D, const StageData& L, const StageDesc& s, float* sL,
+                            float* sPhi, float* sMt, int ldP, const float* sw, const int32_t* bmap, double reg) {
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, w = tid >> 5;
+  const int nv = s.nx + s.nu, nx1 = s.nx1, nb = s.nbu + s.nbx;
+  const int R = nv <= 128 ? 128 : 256, nt = R / 128;
+  // ---- M = [B A]' L_{n+1}: rows i < R of [B A]', columns j < N1 of L
+  const int N1 = (nx1 + 15) & ~15;
+  for (int kc = 0; kc < nx1; kc += kTcK) {
+    for (int e = tid; e < R * kTcK; e += NT) {
+      const int r = e / kTcK, k = e - r * kTcK, kk = kc + k;
+      tc_put(C.tcA, r, k, (r < nv && kk < nx1) ? (float)D[L.BAt + (int64_t)r * L.ldb + kk] : 0.f);
+    }
+    for (int e = tid; e < N1 * kTcK; e += NT) {
+      const int j = e / kTcK, k = e - j * kTcK, kk = kc + k;
+      // B[j][k] = L[k][j] (L lower triangular)
+      tc_put(C.tcB, j, k, (j < nx1 && kk < nx1 && kk >= j) ? sL[kk * nx1 + j] : 0.f);
+    }
+    fence_async_shared();
+    __syncthreads();
+    tc_chunk_mma(C, 0, nt, 0, N1, 0, kc > 0);
+  }
+  // M' from TMEM: warp w reads rows 32 (w % 4) .. of tile w / 4
+  if (w / 4 < nt) {
+    const int t = w / 4, i = t * 128 + 32 * (w & 3) + lane;
+    for (int c0 = 0; c0 < N1; c0 += 16) {
+      float v[16];
+      tc::ld16(C.taddr + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(t * N1 + c0), v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (i < nv && c0 + j < nx1) sMt[(c0 + j) * ldP + i] = v[j];
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  // ---- Phi = M M': column blocks of 128; block cb needs row tiles t >= cb
+  for (int cb = 0; cb * 128 < nv; ++cb) {
+    const int N2 = ((nv - cb * 128 < 128 ? nv - cb * 128 : 128) + 15) & ~15;
+    for (int kc = 0; kc < nx1; kc += kTcK) {
+      for (int e = tid; e < R * kTcK; e += NT) {
+        const int r = e / kTcK, k = e - r * kTcK, kk = kc + k;
+        tc_put(C.tcA, r, k, (r < nv && kk < nx1) ? sMt[kk * ldP + r] : 0.f);
+      }
+      fence_async_shared();
+      __syncthreads();
+      // B = rows cb*128.. of the same tile (M M' is symmetric in its operands)
+      C.tcB = C.tcA;
+      tc_chunk_mma(C, cb, nt, cb * 128, N2, 0, kc > 0);
+      C.tcB = C.tcA + 2 * (tc_tile_bytes() >> 2);
+    }
+    if (w / 4 + cb < nt) {
+      const int t = cb + w / 4, i = t * 128 + 32 * (w & 3) + lane;
+      for (int c0 = 0; c0 < N2; c0 += 16) {
+        float v[16];
+        tc::ld16(C.taddr + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)((t - cb) * N2 + c0), v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int jj = cb * 128 + c0 + j;
+          if (i < nv && jj <= i) {
+            float x = (float)D[L.RSQ + (int64_t)i * L.ldr + jj] + v[j];
+            if (i == jj) {
+              x += (float)reg;
+              if (nb > 0 && bmap[i] >= 0) x += sw[bmap[i]];
+            }
+            sPhi[i * ldP + jj] = x;
+          }
+        }
+      }
+    }
+    tc::fence_before();
+    __syncthreads();
+  }
+}
+
 template <typename Tf>
-__device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
+__device__ bool factor_stage(Ctx& C, int n, const double* D, double reg) {
   const Batch& B = *C.B;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int ldP = block_ld(C.nvmax);
@@ -486,7 +612,20 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
     }
     __syncthreads();
   }
+  bool tc_done = false;
   if constexpr (sizeof(Tf) == 4) {
+    // large stages: both products on the Blackwell tensor cores (tcgen05,
+    // operands in shared memory, accumulators in TMEM)
+    if (C.tc && n < C.N && nv >= 128 && nv <= 256 && nx1 <= 128 && s.ng == 0 && !C.classical && !C.array_qr &&
+        NT == 256) {
+      __syncthreads();
+      tc_products(C, n, D, L, s, reinterpret_cast<float*>(sL), reinterpret_cast<float*>(sPhi),
+                  reinterpret_cast<float*>(sMt), ldP, reinterpret_cast<const float*>(sw), bmap, reg);
+      tc_done = true;
+    }
+  }
+  if constexpr (sizeof(Tf) == 4) {
+    if (!tc_done) {
     // FP32 factor: both products on the tensor cores (3xTF32 mma.sync), each
     // warp owning 16-row strips of 4 n-tiles (16 x 32 outputs)
     const int lane = tid & 31, w = tid >> 5, NW = NT >> 5;
@@ -588,6 +727,7 @@ __device__ bool factor_stage(const Ctx& C, int n, const double* D, double reg) {
       }
     }
     __syncthreads();
+    }
   } else {
   const int nI = (nv + kT - 1) / kT;
     // M' = ([B A]' L_{n+1})': Mt[j][i] = sum_{k >= j} BAt[i][k] L[k][j]
@@ -895,15 +1035,6 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
           [&](int k, int j) { return sL[j * nx1 + k] * (Tf)rb[s.eq + j]; }, [&](int k, Tf v) { va[k] = v; });
     }
     __syncthreads();
-    // general rows' part of the reduced gradient, [D C]' v_g (FP64, row-parallel)
-    double* gtv = C.vbuf + 7 * C.vmax;
-    const bool gen = rd != nullptr && s.ng > 0;
-    if (gen) {
-      rows_dot<double>(
-          nv, [&](int) { return 0; }, [&](int) { return s.ng; },
-          [&](int i, int gg) { return D[L.DC + (int64_t)gg * nv + i] * vs[nb + gg]; },
-          [&](int i, double v) { gtv[i] = v; });
-    }
     if (n < C.N) {
       if (C.classical) {
         // vb = P_{n+1} rb_n + p_{n+1}
@@ -927,7 +1058,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
           [&](int i, Tf v) {
             double gi = g[s.var + i];
             if (rd != nullptr) {
-              if (gen) gi -= gtv[i];
+              for (int gg = 0; gg < s.ng; ++gg) gi = fma(-D[L.DC + (int64_t)gg * nv + i], vs[nb + gg], gi);
               if (nb > 0 && bmap[i] >= 0) gi -= vs[bmap[i]];
             }
             scale = max_nan(scale, fabs(gi));
@@ -1011,10 +1142,8 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
           [&](int k, Tf v) { x1[k] = (double)((Tf)rb[s.eq + k] + v); });
     }
     // dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt) on active sides
-    double* gv = C.vbuf + 6 * C.vmax;
-    general_values(s, L, D, yn, gv);
     for (int c = tid; c < nc; c += NT) {
-      const double v = cons_value(s, L, D, c, yn, gv);
+      const double v = cons_value(s, L, D, c, yn);
       const int il = s.side + c, iu = s.side + nc + c;
       const double dl = rd ? rd[il] : 0.0, du = rd ? rd[iu] : 0.0;
       const double ml = rm ? rm[il] : 0.0, mu = rm ? rm[iu] : 0.0;
@@ -1128,33 +1257,75 @@ __device__ double newton_dir(Ctx& C, const Dir& d, int ir, double ir_tol, Count*
 }
 
 // ---------------------------------------------------------------------------
-// the kernel: one block per QP
+// the kernel: persistent blocks, one QP at a time per block.  Each block takes
+// the next QP of the launch from an atomic counter over `order` (longest
+// QPs first), so long ragged QPs start first and short ones fill the gaps.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch B, const Shape sh,
+__global__ void __launch_bounds__(256, 2) ipm_kernel(const __grid_constant__ Batch B, const Shape sh,
                                                   const __grid_constant__ gq_ipm_arg arg, int kind,
-                                                  double sigma_mu, const DirOut out, const int32_t* order) {
+                                                  double sigma_mu, const DirOut out, const int32_t* order,
+                                                  int count) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int q = order[blockIdx.x];
-  const QpDesc qd = B.qp[q];
   const int tid = threadIdx.x;
   const SmemPlan P = smem_plan(B, sh);
   StageDesc* sst = reinterpret_cast<StageDesc*>(smem + P.stages);
   double* red = reinterpret_cast<double*>(smem + P.red);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P.bars);
   int& s_count = *reinterpret_cast<int*>(smem + P.bars + 2 * sizeof(uint64_t));
-
-  for (int n = tid; n <= qd.N; n += blockDim.x) sst[n] = B.st[qd.stage0 + n];
-  if (tid == 0) {
-    s_count = 0;
-    if (P.staged) {
-      mbar_init(&bars[0], 1);
-      mbar_init(&bars[1], 1);
+  int& s_next = *(reinterpret_cast<int*>(smem + P.bars + 2 * sizeof(uint64_t)) + 1);
+  if (tid == 0 && P.staged) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_async_shared();
+  }
+  Ctx C;
+  C.ring.parity = 0;  // mbarrier phases carry over from one QP to the next
+  C.ring.ok = true;
+  // tensor-core products for large stages in the FP32 factor: one TMEM
+  // allocation per block for the whole launch
+  C.tc = tc_shape(sh) && arg.precision == GQ_PREC_MIXED && blockDim.x == 256 &&
+         kind != (int)LaunchKind::Residuals;
+  C.tcpar = 0;
+  C.taddr = 0;
+  if (C.tc) {
+    C.tcbar = reinterpret_cast<uint64_t*>(smem + P.tcbar);
+    C.tcA = reinterpret_cast<float*>(smem + P.tc);
+    C.tcB = C.tcA + 2 * (tc_tile_bytes() >> 2);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + P.tcbar + 8);
+    if (tid == 0) {
+      mbar_init(C.tcbar, 1);
       fence_async_shared();
     }
+    if (tid < 32) tc::alloc(tslot, kTcCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    C.taddr = *tslot;
+  }
+  for (;;) {
+  __syncthreads();  // the previous QP is done with every shared buffer
+  if (tid == 0) {
+    const int idx = atomicAdd(B.queue + kQueueBlock, 1);
+    s_next = idx < count ? order[idx] : -1;
   }
   __syncthreads();
+  const int q = s_next;
+  if (q < 0) break;
+  if (!C.ring.ok) {
+    // a lost bulk copy left this block's ring in an unknown phase: the QPs
+    // it still takes are reported as timed out instead of solved
+    if (tid == 0) {
+      B.stats[q].status = GQ_STATUS_TIMEOUT;
+      B.stats[q].iters = 0;
+    }
+    continue;
+  }
+  const QpDesc qd = B.qp[q];
 
-  Ctx C;
+  for (int n = tid; n <= qd.N; n += blockDim.x) sst[n] = B.st[qd.stage0 + n];
+  if (tid == 0) s_count = 0;
+  __syncthreads();
+
   C.B = &B;
   C.st = sst;
   C.N = qd.N;
@@ -1177,12 +1348,10 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
   C.ring.buf0 = smem + P.ring0;
   C.ring.slot = (uint32_t)(P.ring1 - P.ring0);
   C.ring.bar = bars;
-  C.ring.parity = 0;
   C.ring.fac_off = (uint32_t)P.ring_fac;
   C.ring.staged = P.staged;
   C.classical = arg.riccati == 1;
   C.array_qr = arg.mode == GQ_MODE_ROBUST;
-  C.ring.ok = true;
 
   // count active sides (integer count: exact in any order)
   {
@@ -1212,7 +1381,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
       stats->res[3] = r.mu;
       if (!C.ring.ok) stats->status = GQ_STATUS_TIMEOUT;
     }
-    return;
+    continue;
   }
 
   if (kind == (int)LaunchKind::NewtonStep) {
@@ -1233,7 +1402,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
       stats->status = !C.ring.ok ? GQ_STATUS_TIMEOUT : (ok ? GQ_STATUS_CONVERGED : GQ_STATUS_NAN);
       stats->ir_total = cnt.ir;
     }
-    return;
+    continue;
   }
 
   // ---------------- full IPM (Sec. 4.2) ----------------
@@ -1251,10 +1420,8 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
       const StageDesc s = sst[n];
       const StageData L = lay(s);
       const int nb = s.nbu + s.nbx, nc = nb + s.ng, nv = s.nx + s.nu;
-      double* gv = C.vbuf + 6 * C.vmax;
-      general_values(s, L, D, B.y + s.var, gv);
       for (int c = tid; c < nc; c += blockDim.x) {
-        const double v = cons_value(s, L, D, c, B.y + s.var, gv);
+        const double v = cons_value(s, L, D, c, B.y + s.var);
         const double lo = D[L.lo + c], hi = D[L.hi + c];
         const int il = s.side + c, iu = s.side + nc + c;
         double sl = 0.0, su = 0.0;  // slacks of a relaxed constraint (Sec. 2.2)
@@ -1486,6 +1653,13 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
     stats->res[2] = r.d;
     stats->res[3] = r.mu;
   }
+  }  // next QP
+  if (C.tc) {
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid < 32) tc::dealloc(C.taddr, kTcCols);
+  }
 }
 
 }  // namespace
@@ -1516,7 +1690,17 @@ cudaError_t launch_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, c
   const int nt = sh.threads > 0 ? sh.threads : 256;
   DirOut o{};
   if (out) o = *out;
-  ipm_kernel<<<count, nt, smem, stream>>>(b, sh, arg, (int)kind, sigma_mu, o, order);
+  // persistent grid: as many blocks as fit the device at once (at most one per QP)
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ipm_kernel, nt, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t resident = (int64_t)(per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
+  const int grid = (int)(count < resident ? count : resident);
+  e = cudaMemsetAsync(b.queue + kQueueBlock, 0, sizeof(int32_t), stream);
+  if (e != cudaSuccess) return e;
+  ipm_kernel<<<grid, nt, smem, stream>>>(b, sh, arg, (int)kind, sigma_mu, o, order, count);
   return cudaGetLastError();
 }
 

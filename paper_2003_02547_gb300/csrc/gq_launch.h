@@ -28,6 +28,18 @@ struct Shape {
 // Column width of the block kernel's Cholesky panels.
 constexpr int kBlockPanel = 8;
 
+// Tensor-core (tcgen05) stage products of the block kernel's FP32 factor:
+// stages with 128 <= nu + nx <= 256, nx_{n+1} <= 128 and no general rows.
+// The operands pass through shared memory in K chunks of kTcK columns (TF32
+// high and low parts of up to 256 rows), the accumulators live in
+// kTcCols TMEM columns per block.
+constexpr int kTcK = 16;
+constexpr int kTcCols = 256;
+__host__ __device__ inline bool tc_shape(const Shape& sh) {
+  return sh.nvmax >= 128 && sh.nvmax <= 256 && sh.nxmax <= 128 && sh.ngmax == 0;
+}
+__host__ __device__ inline size_t tc_tile_bytes() { return (size_t)256 * kTcK * 4; }
+
 // Row stride of the block kernel's Phi and M' tiles: nv rounded up to 4.
 __host__ __device__ inline int block_ld(int nv) { return (nv + 3) & ~3; }
 
@@ -44,7 +56,7 @@ __host__ __device__ inline int64_t block_mat_elems(const Shape& sh) {
 constexpr int kWarpMaxNv = 32;
 
 struct WarpPlan {
-  size_t bars, stages, sL, sM, sP, sv, ring0, ring1, fac_off, bytes;
+  size_t bars, stages, sL, sM, sP, sv, xb, ring0, ring1, fac_off, bytes;
   int vmax;
 };
 WarpPlan warp_plan(const Batch& b, const Shape& sh, int elem);  // elem: factor element size
@@ -55,7 +67,7 @@ constexpr size_t kMaxSmem = 227 * 1024;
 
 // Dynamic shared-memory plan of the IPM kernel (byte offsets).
 struct SmemPlan {
-  size_t bars, red, chunk, vec, mat, panel, stages, ring0, ring1, ring_fac, bytes;
+  size_t bars, red, chunk, vec, mat, panel, stages, tc, tcbar, ring0, ring1, ring_fac, bytes;
   int vmax;
   bool staged;  // stage blocks go through the bulk-copy ring
 };

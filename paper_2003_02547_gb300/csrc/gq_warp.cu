@@ -68,7 +68,21 @@ struct WCtx {
   double* sv;  // per-constraint scratch (vmax doubles)
   int vmax;
   bool qr;     // array algorithm: chol(Ht + M M') by QR of [chol(Ht)'; M']
+  double* xb;  // two 32-entry broadcast buffers (stage vectors read by every lane)
 };
+
+// Stage vector held one element per lane, made readable by every lane from
+// shared memory (buffer k of two): the dot-product loops then issue
+// independent conflict-free loads instead of one dependent shuffle per term.
+// Warp-wide; the barrier before the store keeps earlier readers of the buffer.
+template <typename V>
+__device__ __forceinline__ const V* wbcast(const WCtx& C, int k, V v) {
+  V* buf = reinterpret_cast<V*>(C.xb) + 32 * k;
+  __syncwarp();
+  buf[C.lane] = v;
+  __syncwarp();
+  return buf;
+}
 
 // deterministic sum over this QP's sides: 32-side chunks by butterfly, chunk
 // sums in order (every lane holds the same bits)
@@ -146,28 +160,28 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
   const double yl = lane < nv ? y[s.var + lane] : 0.0;
   const double pl = (n < C.N && lane < nx1) ? pi[s.eq + lane] : 0.0;
   const double* lm = lam + s.side;
+  const double* yv = wbcast<double>(C, 0, yl);
   // r_g, row `lane`
   {
     const double* row = D + L.RSQ + (int64_t)(lane < nv ? lane : 0) * L.ldr;
     double a0 = 0.0, a1 = 0.0;
     int j = 0;
-#pragma unroll 2
+#pragma unroll 4
     for (; j + 1 < nv; j += 2) {
-      const double y0 = __shfl_sync(kFull, yl, j), y1 = __shfl_sync(kFull, yl, j + 1);
-      a0 = fma(row[j], y0, a0);
-      a1 = fma(row[j + 1], y1, a1);
+      a0 = fma(row[j], yv[j], a0);
+      a1 = fma(row[j + 1], yv[j + 1], a1);
     }
-    if (j < nv) a0 = fma(row[j], __shfl_sync(kFull, yl, j), a0);
+    if (j < nv) a0 = fma(row[j], yv[j], a0);
     if (n < C.N) {
+      const double* pv = wbcast<double>(C, 1, pl);
       const double* ba = D + L.BAt + (int64_t)(lane < nv ? lane : 0) * L.ldb;
       int k = 0;
-#pragma unroll 2
+#pragma unroll 4
       for (; k + 1 < nx1; k += 2) {
-        const double p0 = __shfl_sync(kFull, pl, k), p1 = __shfl_sync(kFull, pl, k + 1);
-        a0 = fma(ba[k], p0, a0);
-        a1 = fma(ba[k + 1], p1, a1);
+        a0 = fma(ba[k], pv[k], a0);
+        a1 = fma(ba[k + 1], pv[k + 1], a1);
       }
-      if (k < nx1) a0 = fma(ba[k], __shfl_sync(kFull, pl, k), a0);
+      if (k < nx1) a0 = fma(ba[k], pv[k], a0);
     }
     if (lane < nv) {
       double acc = (lin ? add_g[s.var + lane] : D[L.rq + lane]) + (a0 + a1);
@@ -186,13 +200,12 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
     double a0 = 0.0, a1 = 0.0;
     const int kk = lane < nx1 ? lane : 0;
     int i = 0;
-#pragma unroll 2
+#pragma unroll 4
     for (; i + 1 < nv; i += 2) {
-      const double y0 = __shfl_sync(kFull, yl, i), y1 = __shfl_sync(kFull, yl, i + 1);
-      a0 = fma(D[L.BAt + (int64_t)i * L.ldb + kk], y0, a0);
-      a1 = fma(D[L.BAt + (int64_t)(i + 1) * L.ldb + kk], y1, a1);
+      a0 = fma(D[L.BAt + (int64_t)i * L.ldb + kk], yv[i], a0);
+      a1 = fma(D[L.BAt + (int64_t)(i + 1) * L.ldb + kk], yv[i + 1], a1);
     }
-    if (i < nv) a0 = fma(D[L.BAt + (int64_t)i * L.ldb + kk], __shfl_sync(kFull, yl, i), a0);
+    if (i < nv) a0 = fma(D[L.BAt + (int64_t)i * L.ldb + kk], yv[i], a0);
     if (lane < nx1) {
       const double x1 = y[C.st[n + 1].var + C.st[n + 1].nu + lane];
       const double acc = (lin ? add_b[s.eq + lane] : D[L.b + lane]) + (a0 + a1) - x1;
@@ -210,7 +223,7 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
     for (int c0 = 0; c0 < nc; c0 += 32) {
       const int c = c0 + lane;
       const int src = (c < nb) ? bidx[c] : 0;
-      const double yb = __shfl_sync(kFull, yl, src);
+      const double yb = yv[src];
       if (c < nc) {
         const double v = c < nb ? yb : C.sv[c - nb];
         const double lo = D[L.lo + c], hi = D[L.hi + c];
@@ -571,51 +584,52 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
       scale = max_nan(scale, fabs(rbd));
       const T rbl = (T)rbd;
       // va = L_{n+1}' rb
+      const T* rbv = wbcast<T>(C, 0, rbl);
       T va = T(0);
       #pragma unroll 4
       for (int j = 0; j < nx1; ++j) {
-        const T rj = __shfl_sync(kFull, rbl, j);
-        if (j >= lane) va += sL[j * LDS + (lane < nx1 ? lane : 0)] * rj;
+        if (j >= lane) va += sL[j * LDS + (lane < nx1 ? lane : 0)] * rbv[j];
       }
       // vb = L_{n+1} va + p_{n+1}
+      const T* vav = wbcast<T>(C, 1, va);
       vb = p1;
       #pragma unroll 4
       for (int j = 0; j < nx1; ++j) {
-        const T aj = __shfl_sync(kFull, va, j);
-        if (j <= lane && lane < nx1) vb += sL[lane * LDS + j] * aj;
+        if (j <= lane && lane < nx1) vb += sL[lane * LDS + j] * vav[j];
       }
     }
     // phi = gt + [B A]' vb
     T phi = (T)gi;
     if (n < C.N) {
+      const T* vbv = wbcast<T>(C, 0, vb);
       const T* ba = D + L.BAt + (int64_t)(lane < nv ? lane : 0) * L.ldb;
-            T ph2 = T(0);
+      T ph2 = T(0);
       int k = 0;
-#pragma unroll 2
+#pragma unroll 4
       for (; k + 1 < nx1; k += 2) {
-        const T v0 = __shfl_sync(kFull, vb, k), v1 = __shfl_sync(kFull, vb, k + 1);
-        phi += ba[k] * v0;
-        ph2 += ba[k + 1] * v1;
+        phi += ba[k] * vbv[k];
+        ph2 += ba[k + 1] * vbv[k + 1];
       }
-      if (k < nx1) phi += ba[k] * __shfl_sync(kFull, vb, k);
+      if (k < nx1) phi += ba[k] * vbv[k];
       phi += ph2;
     }
     // l = X phi_e (lanes < ne)
+    const T* phv = wbcast<T>(C, 1, phi);
     T l = T(0);
     {
       const T* xr = F + (int64_t)(lane < ne ? lane : 0) * ldf;
       #pragma unroll 4
       for (int j = 0; j < ne; ++j) {
-        const T pj = __shfl_sync(kFull, phi, j);
-        if (j <= lane) l += xr[j] * pj;
+        if (j <= lane) l += xr[j] * phv[j];
       }
     }
     // p_n = phi_k - L_ke l (lanes < nk)
-    T p = __shfl_sync(kFull, phi, (ne + lane) & 31);
+    T p = phv[(ne + lane) & 31];
     {
+      const T* lv = wbcast<T>(C, 0, l);
       const T* lr = F + (int64_t)(lane < nk ? ne + lane : 0) * ldf;
       #pragma unroll 4
-      for (int j = 0; j < ne; ++j) p -= lr[j] * __shfl_sync(kFull, l, j);
+      for (int j = 0; j < ne; ++j) p -= lr[j] * lv[j];
     }
     if (lane < ne) lp[s.var + lane] = (double)l;
     if (lane < nk) lp[s.var + ne + lane] = (double)p;
@@ -637,19 +651,19 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
     // x_n (lanes ne..nv-1 of the stage vector), written by the previous stage
     const double xd = (lane >= ne && lane < nv) ? dy[s.var + lane] : 0.0;
     const T xl = (T)xd;
+    const T* xv = wbcast<T>(C, 0, xl);
     if (n > 0) {
       // pi_n = L_n (L_n' x_n) + p_n, L_n = L_kk
       T w = T(0);
       #pragma unroll 4
       for (int j = 0; j < nk; ++j) {
-        const T xj = __shfl_sync(kFull, xl, ne + j);
-        if (j >= lane && lane < nk) w += F[(int64_t)(ne + j) * ldf + ne + lane] * xj;
+        if (j >= lane && lane < nk) w += F[(int64_t)(ne + j) * ldf + ne + lane] * xv[ne + j];
       }
+      const T* wv = wbcast<T>(C, 1, w);
       T pk = lane < nk ? (T)lp[s.var + ne + lane] : T(0);
       #pragma unroll 4
       for (int j = 0; j < nk; ++j) {
-        const T wj = __shfl_sync(kFull, w, j);
-        if (j <= lane && lane < nk) pk += F[(int64_t)(ne + lane) * ldf + ne + j] * wj;
+        if (j <= lane && lane < nk) pk += F[(int64_t)(ne + lane) * ldf + ne + j] * wv[j];
       }
       if (lane < nk) dpi[C.st[n - 1].eq + lane] = (double)pk;
     }
@@ -657,32 +671,31 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
     T va = lane < ne ? (T)lp[s.var + lane] : T(0);
     #pragma unroll 4
     for (int i = 0; i < nk; ++i) {
-      const T xi = __shfl_sync(kFull, xl, ne + i);
-      if (lane < ne) va += F[(int64_t)(ne + i) * ldf + lane] * xi;
+      if (lane < ne) va += F[(int64_t)(ne + i) * ldf + lane] * xv[ne + i];
     }
     // u = -X' va
+    const T* vav = wbcast<T>(C, 1, va);
     T u = T(0);
     #pragma unroll 4
     for (int j = 0; j < ne; ++j) {
-      const T aj = __shfl_sync(kFull, va, j);
-      if (j >= lane && lane < ne) u -= F[(int64_t)j * ldf + lane] * aj;
+      if (j >= lane && lane < ne) u -= F[(int64_t)j * ldf + lane] * vav[j];
     }
     const double yd = lane < ne ? (double)u : xd;
     if (lane < ne) dy[s.var + lane] = yd;
     const T yl = (T)yd;
     if (n < C.N) {
       // x_{n+1} = [B A] y_n + rb_n
+      const T* yv = wbcast<T>(C, 0, yl);
       T acc = lane < nx1 ? (T)rb[s.eq + lane] : T(0);
       const int kk = lane < nx1 ? lane : 0;
-            T acc2 = T(0);
+      T acc2 = T(0);
       int i = 0;
-#pragma unroll 2
+#pragma unroll 4
       for (; i + 1 < nv; i += 2) {
-        const T y0 = __shfl_sync(kFull, yl, i), y1 = __shfl_sync(kFull, yl, i + 1);
-        acc += D[L.BAt + (int64_t)i * L.ldb + kk] * y0;
-        acc2 += D[L.BAt + (int64_t)(i + 1) * L.ldb + kk] * y1;
+        acc += D[L.BAt + (int64_t)i * L.ldb + kk] * yv[i];
+        acc2 += D[L.BAt + (int64_t)(i + 1) * L.ldb + kk] * yv[i + 1];
       }
-      if (i < nv) acc += D[L.BAt + (int64_t)i * L.ldb + kk] * __shfl_sync(kFull, yl, i);
+      if (i < nv) acc += D[L.BAt + (int64_t)i * L.ldb + kk] * yv[i];
       acc += acc2;
       if (lane < nx1) dy[C.st[n + 1].var + C.st[n + 1].nu + lane] = (double)acc;
     }
@@ -793,25 +806,45 @@ template <typename T>
 // context in registers, and 12 blocks still fit an SM
 __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B, const WarpPlan P,
                                                       const __grid_constant__ gq_ipm_arg arg, int kind,
-                                                      double sigma_mu, const DirOut out, const int32_t* order) {
+                                                      double sigma_mu, const DirOut out, const int32_t* order,
+                                                      int count, int qslot) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int q = order[blockIdx.x];
-  gq_stats* stats = B.stats + q;
   const bool resume = kind == (int)LaunchKind::Resume;
-  if (resume && stats->status != kStatusResumeFp64) return;  // uniform across the warp
-  const QpDesc qd = B.qp[q];
   const int lane = threadIdx.x;
   StageDesc* sst = reinterpret_cast<StageDesc*>(smem + P.stages);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P.bars);
-  for (int n = lane; n <= qd.N; n += 32) sst[n] = B.st[qd.stage0 + n];
   if (lane == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     fence_async_shared();
   }
+  WCtx C;
+  C.parity = 0;  // mbarrier phases carry over from one QP to the next
+  C.ok = true;
+  // persistent warps: the next QP of the launch from an atomic counter over
+  // `order` (longest first)
+  for (;;) {
+  __syncwarp();
+  int idx = 0;
+  if (lane == 0) idx = atomicAdd(B.queue + qslot, 1);
+  idx = __shfl_sync(kFull, idx, 0);
+  if (idx >= count) break;
+  const int q = order[idx];
+  gq_stats* stats = B.stats + q;
+  if (resume && stats->status != kStatusResumeFp64) continue;  // uniform across the warp
+  if (!C.ok) {
+    // a lost bulk copy left this warp's ring in an unknown phase: the QPs it
+    // still takes are reported as timed out instead of solved
+    if (lane == 0) {
+      stats->status = GQ_STATUS_TIMEOUT;
+      stats->iters = 0;
+    }
+    continue;
+  }
+  const QpDesc qd = B.qp[q];
+  for (int n = lane; n <= qd.N; n += 32) sst[n] = B.st[qd.stage0 + n];
   __syncwarp();
 
-  WCtx C;
   C.B = &B;
   C.st = sst;
   C.N = qd.N;
@@ -825,15 +858,14 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
   C.ring0 = smem + P.ring0;
   C.slot = (uint32_t)(P.ring1 - P.ring0);
   C.bar = bars;
-  C.parity = 0;
   C.fac_off = (uint32_t)P.fac_off;
-  C.ok = true;
   C.sL = smem + P.sL;
   C.sM = smem + P.sM;
   C.sP = smem + P.sP;
   C.sv = reinterpret_cast<double*>(smem + P.sv);
   C.vmax = P.vmax;
   C.qr = arg.mode == GQ_MODE_ROBUST;
+  C.xb = reinterpret_cast<double*>(smem + P.xb);
 
   // active sides (integer count, exact)
   {
@@ -866,7 +898,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
       stats->res[3] = r.mu;
       if (!C.ok) stats->status = GQ_STATUS_TIMEOUT;
     }
-    return;
+    continue;
   }
   if (kind == (int)LaunchKind::NewtonStep) {
     wresiduals(C);
@@ -881,7 +913,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
       stats->status = !C.ok ? GQ_STATUS_TIMEOUT : (ok ? GQ_STATUS_CONVERGED : GQ_STATUS_NAN);
       stats->ir_total = cnt.ir;
     }
-    return;
+    continue;
   }
 
   // ---------------- full IPM (Sec. 4.2) ----------------
@@ -1114,6 +1146,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
     stats->res[2] = r.d;
     stats->res[3] = r.mu;
   }
+  }  // next QP
 }
 
 // FP32 mirror of the stage data blocks: values converted, box indices copied
@@ -1151,6 +1184,7 @@ WarpPlan warp_plan(const Batch& b, const Shape& sh, int elem) {
   p.sM = take((size_t)nv * LDS * te, 16);
   p.sP = take((size_t)nv * LDS * te, 16);
   p.sv = take((size_t)p.vmax * 8, 16);
+  p.xb = take(64 * sizeof(double), 16);
   // ring slot: the FP64 data block (residual sweeps), or a factor-precision
   // data block followed by a factor block (factorisation and solves)
   p.fac_off = ((size_t)sh.data_max * te + 127) / 128 * 128;
@@ -1174,7 +1208,18 @@ static cudaError_t launch_one(const Batch& b, const Shape& sh, const gq_ipm_arg&
     cudaError_t e = cudaFuncSetAttribute(warp_ipm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.bytes);
     if (e != cudaSuccess) return e;
   }
-  warp_ipm_kernel<T><<<count, 32, P.bytes, stream>>>(b, P, arg, (int)kind, sigma_mu, o, order);
+  // persistent grid: as many one-warp blocks as fit the device at once
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_ipm_kernel<T>, 32, P.bytes);
+  if (e != cudaSuccess) return e;
+  const int64_t resident = (int64_t)(per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
+  const int grid = (int)(count < resident ? count : resident);
+  const int qslot = kind == LaunchKind::Resume ? kQueueResume : kQueueWarp;
+  e = cudaMemsetAsync(b.queue + qslot, 0, sizeof(int32_t), stream);
+  if (e != cudaSuccess) return e;
+  warp_ipm_kernel<T><<<grid, 32, P.bytes, stream>>>(b, P, arg, (int)kind, sigma_mu, o, order, count, qslot);
   return cudaGetLastError();
 }
 

@@ -165,6 +165,16 @@ def test_newton_step_mixed_with_refinement_matches_oracle(env):
     _newton_compare(env, qps, precision=1, ir_steps=4, tol=1e-9, ir_tol=1e-12)
 
 
+def test_newton_step_tensor_core_products_match_oracle(env):
+    """Large stages (nu + nx = 192, nx = 128): the FP32 factor's products run
+    on the tcgen05 tensor cores (3xTF32, accumulators in TMEM).  One Newton
+    direction with refinement equals the oracle's at random iterates, and
+    without refinement it is within the FP32 factor's accuracy."""
+    qps = [W.large_stage_qp(i, N=3) for i in range(2)]
+    _newton_compare(env, qps, precision=1, ir_steps=6, tol=1e-9, ir_tol=1e-13)
+    _newton_compare(env, qps, precision=1, ir_steps=0, tol=1e-3)
+
+
 # ----------------------------------------------------------------------------
 # full IPM
 # ----------------------------------------------------------------------------
