@@ -271,6 +271,25 @@ GQ_API int gq_expand(gq_batch* src, int src_qp, int block, const gq_batch* dst, 
                      const double* pi2, const double* lam2, const double* t2, double* y, double* pi, double* lam,
                      double* t);
 
+/* Partial condensing on the device (Sec. 3.5), every QP of a batch at once.
+ * QP q of `src` (uploaded: its device "in" buffer holds the data) is condensed
+ * into QP q of `dst`, which must hold exactly the condensed sizes of
+ * gq_condense_dims for every QP, with private (unshared) stage blocks, and be
+ * attached with its descriptors on the device (gq_upload once after
+ * gq_batch_attach; its data need not be set).  The kernel writes dst's
+ * device data blocks directly (dst's host staging is not updated).  The
+ * arithmetic is that of gq_condense: the Hessian by the backward recursion of
+ * Sec. 3.5 (quadratic in the block length, cubic in the state size), the block
+ * dynamics and the general rows through the forward maps of the block.
+ * dev_ws: caller device memory of at least gq_condense_ws_bytes(src, block)
+ * bytes, 256-byte aligned.  Asynchronous on `stream`.
+ * Errors: GQ_ERR_ARG (NULL, block < 1, soft constraints, shared dst blocks),
+ * GQ_ERR_DIMS (dst sizes), GQ_ERR_SIZE (workspace), GQ_ERR_STATE, GQ_ERR_CUDA.
+ * gq_condense_ws_bytes returns 0 on invalid input. */
+GQ_API size_t gq_condense_ws_bytes(const gq_batch* src, int block);
+GQ_API int gq_condense_device(const gq_batch* src, int block, gq_batch* dst, void* dev_ws, size_t ws_bytes,
+                              void* stream);
+
 /* Getters of the staged problem data, the inverse of the four setters above
  * (same argument meaning and column-major layouts; any output may be NULL;
  * the box getter returns idxbx relative to x).  Errors: GQ_ERR_ARG. */
@@ -395,6 +414,14 @@ GQ_API int gq_get_stats(const gq_batch* b, int qp, gq_stats* out);
 GQ_API int gq_get_statuses(const gq_batch* b, int32_t* status, int32_t* iters);
 
 GQ_API int gq_get_sol_offsets(const gq_batch* b, int qp, int64_t off[8]);
+
+/* ---- measurement helper (no counterpart in the paper) ----
+ * FP32 (fp64 = 0) or FP64 (fp64 = 1) fused multiply-add throughput of the
+ * current device in flop/s, measured by a probe kernel on `stream` with
+ * CUDA events (best of three timed launches after one warm-up).  Benchmarks
+ * use it as the ALU roofline denominator.  Synchronises `stream`.
+ * Errors: GQ_ERR_ARG, GQ_ERR_CUDA. */
+GQ_API int gq_probe_fma_rate(int fp64, void* stream, double* flops_per_s);
 
 /* Per-thread description of the last error, never NULL. */
 GQ_API const char* gq_last_error(void);

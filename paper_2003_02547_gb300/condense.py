@@ -1,5 +1,6 @@
 """Partial condensing through the C ABI (gq_condense_dims, gq_condense,
-gq_expand): argument marshalling only, the condensing runs in libgq."""
+gq_condense_device, gq_expand): argument marshalling only, the condensing
+runs in libgq (host) or in its CUDA kernel (device)."""
 from __future__ import annotations
 
 import ctypes
@@ -28,6 +29,27 @@ def condense(src: QpBatch, indices: Sequence[int], block: int, device: str = "cu
     lib = gq.load()
     for k, i in enumerate(indices):
         gq.check(lib.gq_condense(src.h, int(i), int(block), dst.h, k))
+    return dst
+
+
+def condense_device(src: QpBatch, block: int, stream=None, host_copy: bool = True) -> QpBatch:
+    """Every QP of the uploaded batch ``src`` condensed by ``block`` on the
+    device: a new batch whose device data the condensing kernel writes.  With
+    ``host_copy`` the condensed data are also copied to its host staging (for
+    the host getters); the copy synchronises the stream."""
+    import torch
+    lib = gq.load()
+    dims = [condensed_dims(src, i, block) for i in range(src.nqp)]
+    dst = QpBatch(None, device=src.device, dims=dims)
+    dst.upload(stream)
+    nbytes = int(lib.gq_condense_ws_bytes(src.h, int(block)))
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=src.device)
+    gq.check(lib.gq_condense_device(src.h, int(block), dst.h, ws.data_ptr(), nbytes, src.stream_ptr(stream)))
+    dst._condense_ws = ws   # kept alive with the batch until the kernel has run
+    if host_copy:
+        torch.cuda.synchronize()
+        dst.host_in._np[dst.host_in.off:dst.host_in.off + dst.sizes.in_bytes] = \
+            dst.dev_in[:dst.sizes.in_bytes].cpu().numpy()
     return dst
 
 

@@ -107,6 +107,8 @@ SIGNATURES = {
     "gq_condense": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
     "gq_expand": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, P_double, P_double, P_double, P_double,
                           P_double, P_double, P_double, P_double]),
+    "gq_condense_ws_bytes": (c_size_t, [c_void_p, c_int]),
+    "gq_condense_device": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
     "gq_set_initial_state": (c_int, [c_void_p, c_int, P_double, c_int, P_double, c_int, P_double, P_double, c_int,
                                      P_double, P_double, c_int, P_double, P_double]),
     "gq_copy_qp": (c_int, [c_void_p, c_int, c_void_p, c_int]),
@@ -127,6 +129,7 @@ SIGNATURES = {
     "gq_get_stats": (c_int, [c_void_p, c_int, ctypes.POINTER(Stats)]),
     "gq_get_statuses": (c_int, [c_void_p, P_int, P_int]),
     "gq_get_sol_offsets": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64)]),
+    "gq_probe_fma_rate": (c_int, [c_int, c_void_p, P_double]),
     "gq_last_error": (ctypes.c_char_p, []),
     "gq_server_cfg_default": (c_int, [ctypes.POINTER(ServerCfg)]),
     "gq_server_create": (c_int, [ctypes.POINTER(ServerCfg), c_void_p, c_size_t, c_void_p, c_size_t,
