@@ -72,8 +72,22 @@ def qp_flops(qp):
     return f, s, r
 
 
-P32 = 152 * 128 * 2 * 2.07e9   # FP32 FMA lanes x 2 x max SM clock (flop/s)
-P64 = 1.25e12                  # nominal GB300 FP64 rate (flop/s)
+# ALU peaks (flop/s): measured on the device by the library's FMA probe
+# (gq_probe_fma_rate) when the bench starts; the nominal figures below are
+# kept for reference and used only if the probe fails
+P32_NOMINAL = 152 * 128 * 2 * 2.07e9   # FP32 FMA lanes x 2 x max SM clock
+P64_NOMINAL = 1.25e12                  # nominal GB300 FP64 rate
+PEAKS = {"fp32": P32_NOMINAL, "fp64": P64_NOMINAL, "source": "nominal"}
+
+
+def measure_peaks(stream_ptr) -> None:
+    import ctypes
+    from paper_2003_02547_gb300 import gq
+    lib = gq.load()
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    if lib.gq_probe_fma_rate(0, stream_ptr, ctypes.byref(f32)) == 0 and \
+            lib.gq_probe_fma_rate(1, stream_ptr, ctypes.byref(f64)) == 0 and f32.value > 0 and f64.value > 0:
+        PEAKS.update(fp32=f32.value, fp64=f64.value, source="measured (FMA probe, gq_probe_fma_rate)")
 
 
 def alu_roofline(qps, stats, seconds):
@@ -81,9 +95,9 @@ def alu_roofline(qps, stats, seconds):
     of the flop-mix-weighted ALU peak (FP32 lanes for the FP32 work, the FP64
     rate for the FP64 work)."""
     f32, f64 = work_split(qps, stats)
-    t_min = f32 / P32 + f64 / P64
+    t_min = f32 / PEAKS["fp32"] + f64 / PEAKS["fp64"]
     return {"fp32_tflops": f32 / seconds / 1e12, "fp64_tflops": f64 / seconds / 1e12,
-            "fp32_frac_of_lanes": f32 / seconds / P32, "fp64_frac_of_nominal": f64 / seconds / P64,
+            "fp32_frac_of_peak": f32 / seconds / PEAKS["fp32"], "fp64_frac_of_peak": f64 / seconds / PEAKS["fp64"],
             "frac_of_mix_peak": t_min / seconds if t_min > 0 else None}
 
 
@@ -231,6 +245,8 @@ def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: in
         rep = srv.report()
         infos = [srv.result(t)[0] for t in tickets]
     lat = np.array([inf.latency_ns for inf in infos], dtype=np.float64) * 1e-6
+    done_at = np.array([float(arr[i].t) * 1e3 + lat[i] for i in range(len(arr))])  # ms after t0
+    in_window = int(np.sum(done_at <= duration * 1e3))
     wait = np.array([inf.wait_ns for inf in infos], dtype=np.float64) * 1e-6
     ok = np.array([inf.code == 0 and inf.stats.status == 0 for inf in infos])
     warm = np.array([bool(inf.warm_used) for inf in infos])
@@ -238,7 +254,8 @@ def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: in
     done_last = max(float(arr[i].t) * 1e3 + lat[i] for i in range(len(arr)))
     return {
         "offered_qps": rate, "arrival_s": duration, "requests": len(arr),
-        "throughput_qps": len(arr) / (done_last * 1e-3), "p50_ms": float(np.percentile(lat, 50)),
+        "throughput_qps": len(arr) / (done_last * 1e-3),
+        "served_in_window_qps": in_window / duration, "p50_ms": float(np.percentile(lat, 50)),
         "p99_ms": float(np.percentile(lat, 99)), "admission_wait_share": float(wait.sum() / lat.sum()),
         "converged": int(ok.sum()), "warm_started": int(warm.sum()),
         "not_converged_status": sorted(int(inf.stats.status) for inf in infos if inf.code == 0 and inf.stats.status),
@@ -249,6 +266,10 @@ def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: in
                            "iters": int(inf.stats.iters), "flags": int(inf.stats.flags)}
                           for i, inf in enumerate(infos) if inf.code == 0 and inf.stats.status][:20],
         "rejected_or_failed": int(sum(inf.code != 0 for inf in infos)),
+        # the same QPs solved cold by the CPU oracle: an infeasible QP fails
+        # there too, an IPM failure of the served solve does not
+        "not_converged_oracle": [oracle_status(arr[i].qp) for i, inf in enumerate(infos)
+                                 if inf.code == 0 and inf.stats.status][:5],
         "iters_warm_mean": float(iters[warm].mean()) if warm.any() else None,
         "iters_cold_mean": float(iters[~warm].mean()),
         "iters_warm_hist": np.bincount(iters[warm], minlength=1).tolist() if warm.any() else [],
@@ -259,6 +280,44 @@ def serving_run(rate: float, duration: float, budget_gb: float = 64.0, lanes: in
         "budget_gb": budget_gb, "lanes": lanes, "max_batch": max_batch,
         "wall_s": (t_end - t0) * 1e-9,
     }
+
+
+def oracle_status(qp) -> dict:
+    """Cold oracle solve of one QP at the exit rule of the bench."""
+    from oracle import ocp_ipm as O
+    r = O.solve(qp, O.IpmArg(tol_stat=1e-8, tol_eq=1e-8, tol_ineq=1e-8, tol_comp=1e-8))
+    return {"status": int(r.status), "iters": int(r.iters), "res": [float(x) for x in r.res]}
+
+
+def plain_serving_baseline(dev, sample: int = 48):
+    """The plain per-QP FP64 GPU IPM on the serving request mix: the first
+    `sample` requests of the serving arrivals, each solved alone (one solve
+    call per QP, FP64 Riccati), back to back; solves/s and latency
+    percentiles of the solve calls."""
+    import numpy as np
+    import torch
+    from paper_2003_02547_gb300 import gq, workloads as W
+    from paper_2003_02547_gb300.batch import QpBatch
+    arr = W.serving_arrivals(rate=20000.0, duration=sample / 20000.0 + 1e-3, seed_pool=256)[:sample]
+    arg = gq.default_arg(gq.MODE_SPEED, gq.PREC_FP64)
+    ms, ok = [], 0
+    for x in arr:
+        b = QpBatch([x.qp], device=dev)
+        b.upload()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.solve(arg)
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        b.download()
+        torch.cuda.synchronize()
+        ok += int(b.all_stats()["status"][0] == 0)
+    ms = np.array(ms)
+    return {"value": 1e3 / ms.mean(), "unit": UNIT, "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)), "requests": len(arr), "converged": ok,
+            "note": "cold solves, one QP per solve call; no queueing (a lower bound on its served latency)"}
 
 
 def single_qp_latency(dev, precision: int, solves: int = 10000, graph: bool = False):
@@ -300,19 +359,34 @@ def single_qp_latency(dev, precision: int, solves: int = 10000, graph: bool = Fa
 
 
 def condensed_run(qps, block: int, dev, precision: int, reps: int = 3):
-    """The batch partially condensed by `block` stages (host, libgq) and solved
-    on the device; like the paper's timings the solve is timed alone, and
-    the host condensing time is reported beside it."""
+    """The batch partially condensed by `block` stages on the device
+    (gq_condense_device, one kernel over the uploaded batch) and solved; the
+    condensing kernel and the solve are timed separately with CUDA events,
+    and the host condensing of the same batch is timed beside them."""
+    import ctypes
     import numpy as np
     import torch
     from paper_2003_02547_gb300 import condense as CD, gq
     from paper_2003_02547_gb300.batch import QpBatch
-    src = QpBatch(qps, device=None)
+    src = QpBatch(qps, device=dev)
+    src.upload()
+    dst = CD.condense_device(src, block, host_copy=False)
+    lib = gq.load()
+    nbytes = int(lib.gq_condense_ws_bytes(src.h, block))
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    cms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gq.check(lib.gq_condense_device(src.h, block, dst.h, ws.data_ptr(), nbytes, stream.cuda_stream))
+        e1.record(stream)
+        e1.synchronize()
+        cms.append(e0.elapsed_time(e1))
     t0 = time.perf_counter()
-    dst = CD.condense(src, range(len(qps)), block, device=dev)
-    t_cond = time.perf_counter() - t0
+    CD.condense(QpBatch(qps, device=None), range(len(qps)), block, device=None)
+    t_host = time.perf_counter() - t0
     arg = gq.default_arg(gq.MODE_SPEED, precision)
-    dst.upload()
     dst.solve(arg)
     torch.cuda.synchronize()
     ms = []
@@ -327,8 +401,9 @@ def condensed_run(qps, block: int, dev, precision: int, reps: int = 3):
     torch.cuda.synchronize()
     st = dst.all_stats()
     sch = dst.schedule()
-    return {"block": block, "value": len(qps) / (min(ms) * 1e-3), "unit": UNIT, "ms": min(ms),
-            "host_condense_s": t_cond, "converged": int(np.sum(st["status"] == 0)),
+    return {"block": block, "value": len(qps) / (min(ms) * 1e-3), "unit": UNIT, "solve_ms": min(ms),
+            "device_condense_ms": min(cms), "condense_share_of_solve": min(cms) / min(ms),
+            "host_condense_s": t_host, "converged": int(np.sum(st["status"] == 0)),
             "iters_mean": float(np.mean(st["iters"])), "warp_qps": int(sch.warp_qps), "block_qps": int(sch.block_qps)}
 
 
@@ -460,6 +535,7 @@ def main():
     stream = torch.cuda.current_stream()
     b.upload()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    measure_peaks(stream.cuda_stream)
 
     def barrier():
         if world > 1:
@@ -512,7 +588,7 @@ def main():
     # ---------------- roofline of the IPM kernel ----------------
     f32, f64 = work_split(qps, st)
     t_kernel = mean_ms * 1e-3
-    t_min = f32 / P32 + f64 / P64
+    t_min = f32 / PEAKS["fp32"] + f64 / PEAKS["fp64"]
     achieved = (f32 + f64) / t_kernel
     peak_eff = (f32 + f64) / t_min if t_min > 0 else float("nan")
 
@@ -612,10 +688,19 @@ def main():
         extras["large_stage_256_fp64"] = batch_run(large, dev, gq.PREC_FP64, reps=1)
         del large
         extras["serving"] = serving_run(a.serving_rate, a.serving_duration)
-        # the same request mix below the ragged batch capacity: latency
-        # without a standing queue
-        light = 0.5 * extras["ragged_4096_mixed"]["value"]
-        extras["serving_below_capacity"] = serving_run(light, max(1.0, 600.0 / light))
+        # offered-load sweep over the same request mix: the sustained rate is
+        # the largest offered load the server keeps up with (served rate over
+        # the arrival window at least 90 % of the offered one); latency there
+        # is without a standing queue
+        sweep = []
+        for rate in (100.0, 200.0, 400.0):
+            r = serving_run(rate, 2.0)
+            r["sustained"] = bool(r["served_in_window_qps"] >= 0.9 * rate)
+            sweep.append(r)
+        extras["serving_sweep"] = sweep
+        ok = [r for r in sweep if r["sustained"]]
+        extras["serving_sustained_qps"] = max((r["offered_qps"] for r in ok), default=None)
+        extras["serving_plain_fp64_gpu"] = plain_serving_baseline(dev, sample=48)
         # soft constraints (Sec. 2.2): every state box of the mass-spring batch
         # soft (L2 + L1 penalty); QPs with slacks run in the block kernel, so
         # the hard batch is timed there too.  Reported, not fatal to the line.
@@ -645,7 +730,8 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_eff / 1e12, "unit": "TFLOP/s",
                          "frac": achieved / peak_eff if peak_eff == peak_eff else None, "traffic": captured_traffic(),
                          "kernel": "warp_ipm_kernel<float>", "flops_f32": f32, "flops_f64": f64,
-                         "peak_note": "FP32 152 SMs x 128 lanes x 2 x 2.07 GHz = 80.5 TF; FP64 nominal 1.25 TF; "
+                         "peak_fp32_tflops": PEAKS["fp32"] / 1e12, "peak_fp64_tflops": PEAKS["fp64"] / 1e12,
+                         "peak_note": f"FP32 and FP64 FMA peaks {PEAKS['source']} (nominal 80.5 and 1.25 TF); "
                                       "peak = flop-mix-weighted"},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(b.sizes.in_bytes),
                     "d2h_bytes_per_step": int(b.sizes.sol_bytes), "converged": e2e_ok},
