@@ -698,6 +698,10 @@ def main():
             r["sustained"] = bool(r["served_in_window_qps"] >= 0.9 * rate)
             sweep.append(r)
         extras["serving_sweep"] = sweep
+        # the same 400 QP/s load with 16 lanes (micro-batches in flight)
+        r16 = serving_run(400.0, 2.0, lanes=16)
+        r16["sustained"] = bool(r16["served_in_window_qps"] >= 0.9 * 400.0)
+        extras["serving_400_lanes16"] = r16
         ok = [r for r in sweep if r["sustained"]]
         extras["serving_sustained_qps"] = max((r["offered_qps"] for r in ok), default=None)
         extras["serving_plain_fp64_gpu"] = plain_serving_baseline(dev, sample=48)

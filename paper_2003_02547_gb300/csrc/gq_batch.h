@@ -33,6 +33,7 @@ struct gq_batch {
   int32_t soft_block;   // 1: some QP of the block bucket has slacks (launch the soft kernel variant)
   int32_t warp_max_nv;  // schedule: largest nu + nx (and nx) of a QP run one per warp
   int32_t block_threads;  // schedule: threads per block of the block kernel
+  int32_t tensor_cores;   // schedule: tcgen05 products for large FP32 stages
   gq::Shape shape_w, shape_b;
   gq::QpDesc* qp;
   gq::StageDesc* st;

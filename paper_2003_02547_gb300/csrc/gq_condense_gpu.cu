@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kCondThreads) condense_kernel(const CondArgs a
     for (int i = tid; i < nvp; i += NT) I[nbp + i] = -1;
     __syncthreads();
     if (tid == 0) {
-      int cb = 0, cg = 0, uo = 0;
+      int cb = 0, uo = 0;
       for (int j = 0; j < m; ++j) {
         const StageDesc& s = ss[j];
         const StageData L = stage_data_layout(s);
@@ -279,7 +279,6 @@ __global__ void __launch_bounds__(kCondThreads) condense_kernel(const CondArgs a
         }
       }
       for (int c = 0; c < cb; ++c) I[nbp + I[c]] = c;
-      (void)cg;
     }
     // general rows: the coefficient rows are filled in parallel below; the
     // bounds need the shift of each row and are filled here per row

@@ -234,6 +234,7 @@ void plan_buckets(gq_batch* b) {
   b->shape_b = bucket_shape(b, nw, nqp, false);
   if (nqp > nw) b->shape_b.mat_global = 1;
   b->shape_b.threads = b->block_threads;
+  b->shape_b.tc_off = b->tensor_cores ? 0 : 1;
 }
 
 }  // namespace
@@ -367,6 +368,7 @@ int gq_batch_create_soft(int nqp, const int* dims, size_t dims_len, const int* s
 
   b->warp_max_nv = kWarpMaxNv;
   b->block_threads = 256;
+  b->tensor_cores = 1;
   plan_buckets(b);
   // the block kernel keeps its stage matrices in a per-QP slice of a global
   // scratch region (read through L1/L2): shared memory then holds only
@@ -885,7 +887,7 @@ static int make_kernel_batch_on(const gq_batch* b, void* dev_in, void* dev_sol, 
   k->matg = reinterpret_cast<double*>(ws + L.matg);
   k->queue = reinterpret_cast<int32_t*>(ws + L.queue);
   if (b->nwarp < b->nqp) {
-    const size_t smem = ipm_smem_bytes(*k, b->shape_b);
+    const size_t smem = tc_shape(b->shape_b) ? ipm_tc_smem_bytes(*k, b->shape_b) : ipm_smem_bytes(*k, b->shape_b);
     if (smem > kMaxSmem)
       return fail(GQ_ERR_DIMS,
                   "largest stage (nu+nx=%d, nx=%d) needs %zu bytes of shared memory per block (limit %zu)",
@@ -909,8 +911,13 @@ static cudaError_t launch_all(gq_batch* b, const Batch& k, const gq_ipm_arg& arg
   const int32_t* ord = k.order;
   cudaError_t e = launch_warp_ipm(k, b->shape_w, arg, st, kind, sigma_mu, out, ord, b->nwarp);
   if (e != cudaSuccess) return e;
-  return (b->soft_block ? launch_ipm_soft : launch_ipm)(k, b->shape_b, arg, st, kind, sigma_mu, out, ord + b->nwarp,
-                                                        b->nqp - b->nwarp);
+  // block-kernel variant: slack elimination, tensor-core products of large
+  // FP32 stages, or neither
+  const bool tc = !b->soft_block && tc_shape(b->shape_b) && arg.precision == GQ_PREC_MIXED &&
+                  (b->block_threads == 256);
+  return (b->soft_block ? launch_ipm_soft : (tc ? launch_ipm_tc : launch_ipm))(k, b->shape_b, arg, st, kind,
+                                                                            sigma_mu, out, ord + b->nwarp,
+                                                                            b->nqp - b->nwarp);
 }
 
 static int check_arg(const gq_ipm_arg* a) {
@@ -950,6 +957,7 @@ int gq_get_schedule(const gq_batch* b, gq_schedule* out) {
   if (out == nullptr) return fail(GQ_ERR_ARG, "out is NULL");
   out->warp_max_nv = b->warp_max_nv;
   out->block_threads = b->block_threads;
+  out->tensor_cores = b->tensor_cores;
   out->warp_qps = b->nwarp;
   out->block_qps = b->nqp - b->nwarp;
   return GQ_OK;
@@ -963,8 +971,10 @@ int gq_set_schedule(gq_batch* b, const gq_schedule* sch) {
     return fail(GQ_ERR_ARG, "warp_max_nv must be in 0..%d", kWarpMaxNv);
   if (sch->block_threads != 64 && sch->block_threads != 128 && sch->block_threads != 256)
     return fail(GQ_ERR_ARG, "block_threads must be 64, 128 or 256");
+  if (sch->tensor_cores != 0 && sch->tensor_cores != 1) return fail(GQ_ERR_ARG, "tensor_cores must be 0 or 1");
   b->warp_max_nv = sch->warp_max_nv;
   b->block_threads = sch->block_threads;
+  b->tensor_cores = sch->tensor_cores;
   plan_buckets(b);
   if (b->host_in)
     std::memcpy(static_cast<char*>(b->host_in) + b->L.order, b->order, (size_t)b->nqp * sizeof(int32_t));
@@ -979,26 +989,35 @@ int gq_autotune(gq_batch* b, const gq_ipm_arg* arg, void* stream, int reps, gq_s
   if (reps < 1 || reps > 100) return fail(GQ_ERR_ARG, "reps must be in 1..100");
   if (!b->host_in) return fail(GQ_ERR_STATE, "host_in not attached");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const gq_schedule cands[] = {{kWarpMaxNv, 256, 0, 0}, {kWarpMaxNv, 128, 0, 0}, {0, 256, 0, 0}, {0, 128, 0, 0}};
+  // warp threshold x block threads x tensor-core products
+  gq_schedule cands[4 * 3 * 2];
+  int ncand = 0;
+  for (int wm : {kWarpMaxNv, 24, 16, 0})
+    for (int th : {256, 128, 64})
+      for (int tcs : {1, 0}) cands[ncand++] = gq_schedule{wm, th, 0, 0, tcs};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   double tbest = -1.0;
   gq_schedule sbest = cands[0];
-  int seen_nwarp[4], seen_threads[4], nseen = 0;
-  for (const gq_schedule& c : cands) {
+  int seen_nwarp[4 * 3 * 2], seen_threads[4 * 3 * 2], seen_tc[4 * 3 * 2], nseen = 0;
+  for (int ci = 0; ci < ncand; ++ci) {
+    const gq_schedule& c = cands[ci];
     if (e != cudaSuccess) break;
     gq_schedule probe = c;
     rc = gq_set_schedule(b, &probe);
     if (rc) break;
     // a candidate that runs the same kernels as an earlier one is skipped
-    // (block size without block-bucket QPs)
+    // (block size without block-bucket QPs; tensor cores where no stage uses them)
     const int thr = b->nqp > b->nwarp ? b->block_threads : 0;
+    const int tcu = (b->nqp > b->nwarp && thr == 256 && arg->precision == GQ_PREC_MIXED) ? c.tensor_cores : 0;
     bool dup = false;
-    for (int k = 0; k < nseen; ++k) dup = dup || (seen_nwarp[k] == b->nwarp && seen_threads[k] == thr);
+    for (int k = 0; k < nseen; ++k)
+      dup = dup || (seen_nwarp[k] == b->nwarp && seen_threads[k] == thr && seen_tc[k] == tcu);
     if (dup) continue;
     seen_nwarp[nseen] = b->nwarp;
-    seen_threads[nseen++] = thr;
+    seen_threads[nseen] = thr;
+    seen_tc[nseen++] = tcu;
     rc = gq_upload(b, stream);
     if (rc) break;
     rc = gq_solve(b, arg, stream);  // warm-up

@@ -52,6 +52,14 @@
 #ifndef GQ_IPM_SOFT
 #define GQ_IPM_SOFT 0
 #endif
+// Tensor-core (tcgen05) stage products for large stages: compiled in only
+// when GQ_IPM_TC is 1 (gq_ipm_tc.cu builds this file that way and exports
+// launch_ipm_tc), so that the kernel for other batches keeps its register
+// allocation; the host launches that variant for batches whose block bucket
+// has large FP32 stages.
+#ifndef GQ_IPM_TC
+#define GQ_IPM_TC 0
+#endif
 
 namespace gq {
 
@@ -74,7 +82,7 @@ __host__ __device__ SmemPlan smem_plan(const Batch& b, const Shape& sh) {
   p.stages = take((size_t)sh.nst_max * sizeof(StageDesc), 16);
   // tensor-core operand tiles (TF32 high and low parts of A and of B), the
   // MMA-completion mbarrier and the TMEM address
-  if (tc_shape(sh)) {
+  if (GQ_IPM_TC && tc_shape(sh)) {
     p.tc = take(4 * tc_tile_bytes(), 1024);
     p.tcbar = take(16, 16);
   } else {
@@ -258,16 +266,26 @@ __device__ __forceinline__ Tf* fac_global(const Batch& B, const StageDesc& s) {
   return reinterpret_cast<Tf*>(static_cast<double*>(B.fac) + s.fac);
 }
 
-// value of constraint c of stage s at the stage vector y (length nv)
+// values of the general rows [D C] y of stage s (FP64, row-parallel dot
+// products with short dependent chains) into gv[ng]; block-wide, ends with a
+// barrier when ng > 0.  Every thread of the block must call it.
+__device__ __forceinline__ void general_values(const StageDesc& s, const StageData& L, const double* D,
+                                               const double* y, double* gv) {
+  const int nv = s.nx + s.nu;
+  if (s.ng > 0) {  // uniform across the block
+    rows_dot<double>(
+        s.ng, [&](int) { return 0; }, [&](int) { return nv; },
+        [&](int g, int j) { return D[L.DC + (int64_t)g * nv + j] * y[j]; }, [&](int g, double v) { gv[g] = v; });
+    __syncthreads();
+  }
+}
+
+// value of constraint c of stage s at y, general rows from general_values
 __device__ __forceinline__ double cons_value(const StageDesc& s, const StageData& L, const double* D, int c,
-                                                    const double* y) {
+                                             const double* y, const double* gv) {
   const int nb = s.nbu + s.nbx;
   if (c < nb) return y[box_idx(D, L)[c]];
-  const int nv = s.nx + s.nu;
-  const double* row = D + L.DC + (int64_t)(c - nb) * nv;
-  double v = 0.0;
-  for (int j = 0; j < nv; ++j) v = fma(row[j], y[j], v);
-  return v;
+  return gv[c - nb];
 }
 
 // ---------------------------------------------------------------------------
@@ -346,17 +364,18 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
   // r_g rows: [RSQ row | [B A]' row] . [y_n | pi_{n+1}], then the rest
   {
     const double* pn1 = pi + s.eq;
-    const int kend = n < C.N ? nv + nx1 : nv;
+    const int kdyn = n < C.N ? nv + nx1 : nv;  // then the ng general-row terms
     rows_dot<double>(
-        nv, [&](int) { return 0; }, [&](int) { return kend; },
+        nv, [&](int) { return 0; }, [&](int) { return kdyn + s.ng; },
         [&](int i, int k) {
-          return k < nv ? D[L.RSQ + (int64_t)i * L.ldr + k] * yn[k] : D[L.BAt + (int64_t)i * L.ldb + (k - nv)] * pn1[k - nv];
+          if (k < nv) return D[L.RSQ + (int64_t)i * L.ldr + k] * yn[k];
+          if (k < kdyn) return D[L.BAt + (int64_t)i * L.ldb + (k - nv)] * pn1[k - nv];
+          const int g = k - kdyn;
+          return -D[L.DC + (int64_t)g * nv + i] * (lm[nb + g] - lm[nc + nb + g]);
         },
         [&](int i, double v) {
           double acc = (lin ? add_g[s.var + i] : D[L.rq + i]) + v;
           if (n > 0 && i >= s.nu) acc -= pi[C.st[n - 1].eq + (i - s.nu)];
-          for (int g = 0; g < s.ng; ++g)
-            acc = fma(-D[L.DC + (int64_t)g * nv + i], lm[nb + g] - lm[nc + nb + g], acc);
           if (nb > 0) {
             const int c = bmap[i];
             if (c >= 0) acc -= lm[c] - lm[nc + c];
@@ -377,8 +396,10 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
         });
   }
   if (rd != nullptr) {
+    double* gv = C.vbuf + 6 * C.vmax;
+    general_values(s, L, D, yn, gv);
     for (int c = tid; c < nc; c += NT) {
-      const double v = cons_value(s, L, D, c, yn);
+      const double v = cons_value(s, L, D, c, yn, gv);
       const double lo = D[L.lo + c], hi = D[L.hi + c];
       const int il = s.side + c, iu = s.side + nc + c;
       double a = 0.0, b = 0.0;
@@ -452,6 +473,7 @@ __device__ __forceinline__ void tri_tile(int t, int& I, int& J) {
   J = t - i * (i + 1) / 2;
 }
 
+#if GQ_IPM_TC
 // ---------------------------------------------------------------------------
 // Tensor-core stage products of the FP32 factor (tcgen05, Blackwell):
 //   M = [B A]' L_{n+1}          (nv x nx1, stored transposed as M')
@@ -502,7 +524,7 @@ __device__ __forceinline__ void tc_chunk_mma(Ctx& C, int t0, int t1, int brow, i
   tc::fence_after();
 }
 
-__device__ void tc_products(Ctx& C, int n, const double* D, const StageData& L, const StageDesc& s, float* sL,
+__device__ __noinline__ void tc_products(Ctx& C, int n, const double* D, const StageData& L, const StageDesc& s, float* sL,
                             float* sPhi, float* sMt, int ldP, const float* sw, const int32_t* bmap, double reg) {
   const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, w = tid >> 5;
   const int nv = s.nx + s.nu, nx1 = s.nx1, nb = s.nbu + s.nbx;
@@ -575,6 +597,8 @@ __device__ void tc_products(Ctx& C, int n, const double* D, const StageData& L, 
   }
 }
 
+#endif  // GQ_IPM_TC
+
 template <typename Tf>
 __device__ bool factor_stage(Ctx& C, int n, const double* D, double reg) {
   const Batch& B = *C.B;
@@ -613,6 +637,7 @@ __device__ bool factor_stage(Ctx& C, int n, const double* D, double reg) {
     __syncthreads();
   }
   bool tc_done = false;
+#if GQ_IPM_TC
   if constexpr (sizeof(Tf) == 4) {
     // large stages: both products on the Blackwell tensor cores (tcgen05,
     // operands in shared memory, accumulators in TMEM)
@@ -624,6 +649,7 @@ __device__ bool factor_stage(Ctx& C, int n, const double* D, double reg) {
       tc_done = true;
     }
   }
+#endif
   if constexpr (sizeof(Tf) == 4) {
     if (!tc_done) {
     // FP32 factor: both products on the tensor cores (3xTF32 mma.sync), each
@@ -1035,6 +1061,15 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
           [&](int k, int j) { return sL[j * nx1 + k] * (Tf)rb[s.eq + j]; }, [&](int k, Tf v) { va[k] = v; });
     }
     __syncthreads();
+    // general rows' part of the reduced gradient, [D C]' v_g (FP64, row-parallel)
+    double* gtv = C.vbuf + 7 * C.vmax;
+    const bool gen = rd != nullptr && s.ng > 0;
+    if (gen) {
+      rows_dot<double>(
+          nv, [&](int) { return 0; }, [&](int) { return s.ng; },
+          [&](int i, int gg) { return D[L.DC + (int64_t)gg * nv + i] * vs[nb + gg]; },
+          [&](int i, double v) { gtv[i] = v; });
+    }
     if (n < C.N) {
       if (C.classical) {
         // vb = P_{n+1} rb_n + p_{n+1}
@@ -1058,7 +1093,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
           [&](int i, Tf v) {
             double gi = g[s.var + i];
             if (rd != nullptr) {
-              for (int gg = 0; gg < s.ng; ++gg) gi = fma(-D[L.DC + (int64_t)gg * nv + i], vs[nb + gg], gi);
+              if (gen) gi -= gtv[i];
               if (nb > 0 && bmap[i] >= 0) gi -= vs[bmap[i]];
             }
             scale = max_nan(scale, fabs(gi));
@@ -1142,8 +1177,10 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
           [&](int k, Tf v) { x1[k] = (double)((Tf)rb[s.eq + k] + v); });
     }
     // dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt) on active sides
+    double* gv = C.vbuf + 6 * C.vmax;
+    general_values(s, L, D, yn, gv);
     for (int c = tid; c < nc; c += NT) {
-      const double v = cons_value(s, L, D, c, yn);
+      const double v = cons_value(s, L, D, c, yn, gv);
       const int il = s.side + c, iu = s.side + nc + c;
       const double dl = rd ? rd[il] : 0.0, du = rd ? rd[iu] : 0.0;
       const double ml = rm ? rm[il] : 0.0, mu = rm ? rm[iu] : 0.0;
@@ -1257,75 +1294,33 @@ __device__ double newton_dir(Ctx& C, const Dir& d, int ir, double ir_tol, Count*
 }
 
 // ---------------------------------------------------------------------------
-// the kernel: persistent blocks, one QP at a time per block.  Each block takes
-// the next QP of the launch from an atomic counter over `order` (longest
-// QPs first), so long ragged QPs start first and short ones fill the gaps.
+// the kernel: one block per QP
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 2) ipm_kernel(const __grid_constant__ Batch B, const Shape sh,
+__global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch B, const Shape sh,
                                                   const __grid_constant__ gq_ipm_arg arg, int kind,
-                                                  double sigma_mu, const DirOut out, const int32_t* order,
-                                                  int count) {
+                                                  double sigma_mu, const DirOut out, const int32_t* order) {
   extern __shared__ __align__(128) unsigned char smem[];
+  const int q = order[blockIdx.x];
+  const QpDesc qd = B.qp[q];
   const int tid = threadIdx.x;
   const SmemPlan P = smem_plan(B, sh);
   StageDesc* sst = reinterpret_cast<StageDesc*>(smem + P.stages);
   double* red = reinterpret_cast<double*>(smem + P.red);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P.bars);
   int& s_count = *reinterpret_cast<int*>(smem + P.bars + 2 * sizeof(uint64_t));
-  int& s_next = *(reinterpret_cast<int*>(smem + P.bars + 2 * sizeof(uint64_t)) + 1);
-  if (tid == 0 && P.staged) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    fence_async_shared();
-  }
-  Ctx C;
-  C.ring.parity = 0;  // mbarrier phases carry over from one QP to the next
-  C.ring.ok = true;
-  // tensor-core products for large stages in the FP32 factor: one TMEM
-  // allocation per block for the whole launch
-  C.tc = tc_shape(sh) && arg.precision == GQ_PREC_MIXED && blockDim.x == 256 &&
-         kind != (int)LaunchKind::Residuals;
-  C.tcpar = 0;
-  C.taddr = 0;
-  if (C.tc) {
-    C.tcbar = reinterpret_cast<uint64_t*>(smem + P.tcbar);
-    C.tcA = reinterpret_cast<float*>(smem + P.tc);
-    C.tcB = C.tcA + 2 * (tc_tile_bytes() >> 2);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + P.tcbar + 8);
-    if (tid == 0) {
-      mbar_init(C.tcbar, 1);
-      fence_async_shared();
-    }
-    if (tid < 32) tc::alloc(tslot, kTcCols);
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    C.taddr = *tslot;
-  }
-  for (;;) {
-  __syncthreads();  // the previous QP is done with every shared buffer
-  if (tid == 0) {
-    const int idx = atomicAdd(B.queue + kQueueBlock, 1);
-    s_next = idx < count ? order[idx] : -1;
-  }
-  __syncthreads();
-  const int q = s_next;
-  if (q < 0) break;
-  if (!C.ring.ok) {
-    // a lost bulk copy left this block's ring in an unknown phase: the QPs
-    // it still takes are reported as timed out instead of solved
-    if (tid == 0) {
-      B.stats[q].status = GQ_STATUS_TIMEOUT;
-      B.stats[q].iters = 0;
-    }
-    continue;
-  }
-  const QpDesc qd = B.qp[q];
 
   for (int n = tid; n <= qd.N; n += blockDim.x) sst[n] = B.st[qd.stage0 + n];
-  if (tid == 0) s_count = 0;
+  if (tid == 0) {
+    s_count = 0;
+    if (P.staged) {
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      fence_async_shared();
+    }
+  }
   __syncthreads();
 
+  Ctx C;
   C.B = &B;
   C.st = sst;
   C.N = qd.N;
@@ -1348,10 +1343,35 @@ __global__ void __launch_bounds__(256, 2) ipm_kernel(const __grid_constant__ Bat
   C.ring.buf0 = smem + P.ring0;
   C.ring.slot = (uint32_t)(P.ring1 - P.ring0);
   C.ring.bar = bars;
+  C.ring.parity = 0;
   C.ring.fac_off = (uint32_t)P.ring_fac;
   C.ring.staged = P.staged;
   C.classical = arg.riccati == 1;
   C.array_qr = arg.mode == GQ_MODE_ROBUST;
+  C.ring.ok = true;
+  // tensor-core products for large stages in the FP32 factor: one TMEM
+  // allocation per block
+  C.tc = GQ_IPM_TC && tc_shape(sh) && arg.precision == GQ_PREC_MIXED && blockDim.x == 256 &&
+         kind != (int)LaunchKind::Residuals;
+  C.tcpar = 0;
+  C.taddr = 0;
+#if GQ_IPM_TC
+  if (C.tc) {
+    C.tcbar = reinterpret_cast<uint64_t*>(smem + P.tcbar);
+    C.tcA = reinterpret_cast<float*>(smem + P.tc);
+    C.tcB = C.tcA + 2 * (tc_tile_bytes() >> 2);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + P.tcbar + 8);
+    if (tid == 0) {
+      mbar_init(C.tcbar, 1);
+      fence_async_shared();
+    }
+    if (tid < 32) tc::alloc(tslot, kTcCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    C.taddr = *tslot;
+  }
+#endif
 
   // count active sides (integer count: exact in any order)
   {
@@ -1381,7 +1401,7 @@ __global__ void __launch_bounds__(256, 2) ipm_kernel(const __grid_constant__ Bat
       stats->res[3] = r.mu;
       if (!C.ring.ok) stats->status = GQ_STATUS_TIMEOUT;
     }
-    continue;
+    return;
   }
 
   if (kind == (int)LaunchKind::NewtonStep) {
@@ -1402,7 +1422,15 @@ __global__ void __launch_bounds__(256, 2) ipm_kernel(const __grid_constant__ Bat
       stats->status = !C.ring.ok ? GQ_STATUS_TIMEOUT : (ok ? GQ_STATUS_CONVERGED : GQ_STATUS_NAN);
       stats->ir_total = cnt.ir;
     }
-    continue;
+#if GQ_IPM_TC
+    if (C.tc) {
+      tc::fence_before();
+      __syncthreads();
+      tc::fence_after();
+      if (tid < 32) tc::dealloc(C.taddr, kTcCols);
+    }
+#endif
+    return;
   }
 
   // ---------------- full IPM (Sec. 4.2) ----------------
@@ -1420,8 +1448,10 @@ __global__ void __launch_bounds__(256, 2) ipm_kernel(const __grid_constant__ Bat
       const StageDesc s = sst[n];
       const StageData L = lay(s);
       const int nb = s.nbu + s.nbx, nc = nb + s.ng, nv = s.nx + s.nu;
+      double* gv = C.vbuf + 6 * C.vmax;
+      general_values(s, L, D, B.y + s.var, gv);
       for (int c = tid; c < nc; c += blockDim.x) {
-        const double v = cons_value(s, L, D, c, B.y + s.var);
+        const double v = cons_value(s, L, D, c, B.y + s.var, gv);
         const double lo = D[L.lo + c], hi = D[L.hi + c];
         const int il = s.side + c, iu = s.side + nc + c;
         double sl = 0.0, su = 0.0;  // slacks of a relaxed constraint (Sec. 2.2)
@@ -1653,18 +1683,24 @@ __global__ void __launch_bounds__(256, 2) ipm_kernel(const __grid_constant__ Bat
     stats->res[2] = r.d;
     stats->res[3] = r.mu;
   }
-  }  // next QP
+#if GQ_IPM_TC
   if (C.tc) {
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     if (tid < 32) tc::dealloc(C.taddr, kTcCols);
   }
+#endif
 }
 
 }  // namespace
 
-#if GQ_IPM_SOFT
+#if GQ_IPM_TC
+size_t ipm_tc_smem_bytes(const Batch& b, const Shape& sh) { return smem_plan(b, sh).bytes; }
+
+cudaError_t launch_ipm_tc(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
+                          LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count) {
+#elif GQ_IPM_SOFT
 cudaError_t launch_ipm_soft(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
                             LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count) {
 #else
@@ -1674,7 +1710,7 @@ cudaError_t launch_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, c
                        LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count) {
 #endif
   if (count <= 0) return cudaSuccess;
-  const size_t smem = ipm_smem_bytes(b, sh);
+  const size_t smem = GQ_IPM_TC ? smem_plan(b, sh).bytes : ipm_smem_bytes(b, sh);
   if (smem > kMaxSmem) return cudaErrorInvalidConfiguration;
   // opt in to the dynamic shared memory this launch needs (set on the current
   // device at every launch above the default: no cache shared between host
@@ -1690,17 +1726,7 @@ cudaError_t launch_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, c
   const int nt = sh.threads > 0 ? sh.threads : 256;
   DirOut o{};
   if (out) o = *out;
-  // persistent grid: as many blocks as fit the device at once (at most one per QP)
-  int dev = 0, nsm = 0, per_sm = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ipm_kernel, nt, smem);
-  if (e != cudaSuccess) return e;
-  const int64_t resident = (int64_t)(per_sm > 0 ? per_sm : 1) * (nsm > 0 ? nsm : 1);
-  const int grid = (int)(count < resident ? count : resident);
-  e = cudaMemsetAsync(b.queue + kQueueBlock, 0, sizeof(int32_t), stream);
-  if (e != cudaSuccess) return e;
-  ipm_kernel<<<grid, nt, smem, stream>>>(b, sh, arg, (int)kind, sigma_mu, o, order, count);
+  ipm_kernel<<<count, nt, smem, stream>>>(b, sh, arg, (int)kind, sigma_mu, o, order);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ struct Shape {
   int64_t data_max;  // largest stage data block (elements)
   int32_t mat_global;  // block kernel: stage matrices in the global workspace (too large for shared memory)
   int32_t threads;     // block kernel: threads per block (0: 256)
+  int32_t tc_off;      // block kernel: no tensor-core (tcgen05) products
 };
 
 // Column width of the block kernel's Cholesky panels.
@@ -36,7 +37,7 @@ constexpr int kBlockPanel = 8;
 constexpr int kTcK = 16;
 constexpr int kTcCols = 256;
 __host__ __device__ inline bool tc_shape(const Shape& sh) {
-  return sh.nvmax >= 128 && sh.nvmax <= 256 && sh.nxmax <= 128 && sh.ngmax == 0;
+  return !sh.tc_off && sh.nvmax >= 128 && sh.nvmax <= 256 && sh.nxmax <= 128 && sh.ngmax == 0;
 }
 __host__ __device__ inline size_t tc_tile_bytes() { return (size_t)256 * kTcK * 4; }
 
@@ -78,6 +79,10 @@ size_t ipm_smem_bytes(const Batch& b, const Shape& sh);
 
 cudaError_t launch_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
                        LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count);
+// the same with the tensor-core products of large FP32 stages compiled in
+size_t ipm_tc_smem_bytes(const Batch& b, const Shape& sh);
+cudaError_t launch_ipm_tc(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
+                          LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count);
 // the same with the slack elimination of soft constraints compiled in
 cudaError_t launch_ipm_soft(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
                        LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count);

@@ -84,16 +84,14 @@ __device__ __forceinline__ const V* wbcast(const WCtx& C, int k, V v) {
   return buf;
 }
 
-// deterministic sum over this QP's sides: 32-side chunks by butterfly, chunk
-// sums in order (every lane holds the same bits)
+// deterministic sum over this QP's sides: each lane sums its sides in index
+// order, then one butterfly (every lane holds the same bits)
 template <class F>
 __device__ __forceinline__ double side_sum(const WCtx& C, F f) {
   double acc = 0.0;
-  for (int c0 = 0; c0 < C.nside; c0 += 32) {
-    const int k = c0 + C.lane;
-    acc += warp_sum(k < C.nside ? f(C.side0 + k) : 0.0);
-  }
-  return acc;
+#pragma unroll 4
+  for (int k = C.lane; k < C.nside; k += 32) acc += f(C.side0 + k);
+  return warp_sum(acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -764,8 +762,11 @@ __device__ double wnewton(WCtx& C, const WDir& d, int ir, double ir_tol, WCount*
     cnt->m = m;
     if (k == ir || m <= ir_tol * mr) break;
     wsolve<T>(C, B.rg2, nullptr, nullptr, B.rb2, B.dy2, B.dpi2, B.dlam2, B.dt2);
+    #pragma unroll 4
     for (int i = C.v0 + C.lane; i < C.v1; i += 32) d.dy[i] += B.dy2[i];
+    #pragma unroll 4
     for (int i = C.e0 + C.lane; i < C.e1; i += 32) d.dpi[i] += B.dpi2[i];
+    #pragma unroll 4
     for (int i = C.side0 + C.lane; i < C.side0 + C.nside; i += 32) {
       d.dlam[i] += B.dlam2[i];
       d.dt[i] += B.dt2[i];
@@ -780,6 +781,7 @@ __device__ double wnewton(WCtx& C, const WDir& d, int ir, double ir_tol, WCount*
 __device__ double wmax_step(const WCtx& C, const double* dlam, const double* dt) {
   const Batch& B = *C.B;
   double a = INFINITY;
+  #pragma unroll 4
   for (int i = C.side0 + C.lane; i < C.side0 + C.nside; i += 32) {
     if (dlam[i] < 0.0) a = fmin(a, -B.lam[i] / dlam[i]);
     if (dt[i] < 0.0) a = fmin(a, -B.t[i] / dt[i]);
@@ -885,6 +887,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
   const bool mixed = arg.precision == GQ_PREC_MIXED;
   // 1/t on every side (masked sides: t = 1)
   auto set_tinv = [&]() {
+    #pragma unroll 4
     for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) B.tinv[i] = 1.0 / B.t[i];
     __syncwarp();
   };
@@ -902,6 +905,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
   }
   if (kind == (int)LaunchKind::NewtonStep) {
     wresiduals(C);
+    #pragma unroll 4
     for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32)
       B.rm[i] = B.lam[i] * B.t[i] - (B.lam[i] != 0.0 ? sigma_mu : 0.0);
     set_tinv();
@@ -922,7 +926,9 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
     const int wlev = qd.warm > 0 ? qd.warm - 1 : arg.warm_start;
     const bool warm1 = wlev >= 1, warm2 = wlev >= 2;
     if (!warm1) {
+      #pragma unroll 4
       for (int i = C.v0 + lane; i < C.v1; i += 32) B.y[i] = 0.0;
+      #pragma unroll 4
       for (int i = C.e0 + lane; i < C.e1; i += 32) B.pi[i] = 0.0;
     }
     __syncwarp();
@@ -1024,6 +1030,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
         break;
       }
     }
+    #pragma unroll 4
     for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) B.rm[i] = B.lam[i] * B.t[i];
     set_tinv();
     const double reg = fp64 ? (mixed ? 0.0 : arg.reg_prim) : arg.reg_prim;
@@ -1048,6 +1055,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
       lifted_at = it;
       const double floor_lt = fmax(kLift, kLiftRel * fmax(r.g, r.b));
       flags |= GQ_FLAG_REGULARIZED;
+      #pragma unroll 4
       for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) {
         if (B.lam[i] != 0.0) {
           B.lam[i] = fmax(B.lam[i], floor_lt);
@@ -1075,6 +1083,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
       const double mu_aff = wmu_after(C, a_aff, d.dlam, d.dt);
       const double sigma = r.mu > 0.0 ? (mu_aff / r.mu) * (mu_aff / r.mu) * (mu_aff / r.mu) : 0.0;
       const double smu = sigma * r.mu;
+      #pragma unroll 4
       for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32)
         B.rm[i] = B.lam[i] != 0.0 ? B.lam[i] * B.t[i] + d.dlam[i] * d.dt[i] - smu : 0.0;
       __syncwarp();
@@ -1083,6 +1092,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
         const double a_c = fmin(1.0, wmax_step(C, d.dlam, d.dt));
         const double mu_c = wmu_after(C, a_c, d.dlam, d.dt);
         if (mu_c > arg.corr_k * mu_aff) {
+          #pragma unroll 4
           for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32)
             B.rm[i] = B.lam[i] != 0.0 ? B.lam[i] * B.t[i] - smu : 0.0;
           __syncwarp();
@@ -1121,8 +1131,11 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
       }
       alpha = 1.0;
     }
+    #pragma unroll 4
     for (int i = C.v0 + lane; i < C.v1; i += 32) B.y[i] += alpha * d.dy[i];
+    #pragma unroll 4
     for (int i = C.e0 + lane; i < C.e1; i += 32) B.pi[i] += alpha * d.dpi[i];
+    #pragma unroll 4
     for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) {
       if (B.lam[i] != 0.0 || d.dlam[i] != 0.0) {
         B.lam[i] = fmax(B.lam[i] + alpha * d.dlam[i], arg.lam_min);

@@ -51,7 +51,7 @@ class Sizes(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("warp_max_nv", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("warp_qps", ctypes.c_int32), ("block_qps", ctypes.c_int32)]
+                ("warp_qps", ctypes.c_int32), ("block_qps", ctypes.c_int32), ("tensor_cores", ctypes.c_int32)]
 
 
 class ServerCfg(ctypes.Structure):

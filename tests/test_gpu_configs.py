@@ -95,3 +95,21 @@ def test_large_stage_full_batch(env, precision):
         kkt = O.full_residuals(qps[i], y, pi, lam, t)
         assert max(kkt[:4]) <= GP.KKT_TOL * 1.01, (i, kkt)
         assert np.all(lam >= 0) and np.all(t > 0)
+
+
+def test_large_stage_with_and_without_tensor_cores(env):
+    """The same large-stage QPs (nu + nx = 192) in the mixed path with the
+    tcgen05 products (schedule tensor_cores = 1) and with the warp-level
+    mma.sync products (0): both meet the oracle gates."""
+    gq, QpBatch, torch = env
+    qps = [W.large_stage_qp(i, N=6) for i in range(2)]
+    for tc in (1, 0):
+        b = QpBatch(qps)
+        b.set_schedule(32, 256, tc)
+        assert b.schedule().tensor_cores == tc
+        b.upload()
+        b.solve(gq.default_arg(0, 1))
+        b.download()
+        torch.cuda.synchronize()
+        assert np.all(b.all_stats()["status"] == 0), (tc, b.all_stats())
+        check_sample(b, qps, range(len(qps)), 1)
