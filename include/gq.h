@@ -334,14 +334,18 @@ typedef struct gq_schedule {
     int32_t block_threads; /* threads per block of the block kernel: 64, 128 or 256    */
     int32_t warp_qps;      /* out: QPs in the warp bucket                             */
     int32_t block_qps;     /* out: QPs in the block bucket                            */
-    int32_t tensor_cores;  /* 1: FP32 factors of large stages (128 <= nu + nx <= 256,
+    int32_t tensor_cores;  /* FP32 factors of large stages (128 <= nu + nx <= 256,
                               nx <= 128, no general rows, 256 threads) form their
                               products on the tcgen05 tensor cores (TF32 operands in
-                              shared memory, accumulators in tensor memory); 0: the
-                              warp-level mma.sync products                              */
+                              shared memory, accumulators in tensor memory) when this
+                              is 2, or when it is 1 and the block bucket holds at most
+                              one QP per two SMs (measured: once blocks share SMs the
+                              operand tiles' shared memory costs more than the
+                              products gain); 0: always the warp-level mma.sync
+                              products                                                  */
 } gq_schedule;
 
-/* Defaults: warp_max_nv 32, block_threads 256, tensor_cores 1. */
+/* Defaults: warp_max_nv 32, block_threads 256, tensor_cores 1 (automatic). */
 GQ_API int gq_get_schedule(const gq_batch* b, gq_schedule* out);
 
 /* Re-plans the buckets (host handle and host "in" staging); gq_upload before
@@ -353,7 +357,7 @@ GQ_API int gq_set_schedule(gq_batch* b, const gq_schedule* sch);
  * buffers overwritten) under each distinct candidate schedule -- warp
  * threshold 32, 24, 16 or 0 (one QP per warp for stages up to that size,
  * one block per QP for the rest), 256, 128 or 64 threads per block, tensor-
- * core products on or off -- keeps the fastest, uploads it and returns it
+ * core products on (2) or off (0) -- keeps the fastest, uploads it and returns it
  * (and its mean solve time in ms).  Candidates that run the same kernels as
  * an earlier one are skipped.  Blocks until the timing solves finish (it synchronises `stream`).
  * Errors: as gq_solve, GQ_ERR_CUDA for event failures. */

@@ -139,8 +139,7 @@ __device__ double block_reduce(double v, double* red, Op op) {
 // per-block context
 // ---------------------------------------------------------------------------
 struct Ring {
-  unsigned char* buf0;  // two consecutive slots of `slot` bytes (no indexed array)
-  uint32_t slot;
+  unsigned char* buf[2];
   uint64_t* bar;     // two mbarriers
   uint32_t parity;   // bit b: parity of the next phase of buffer b
   uint32_t fac_off;  // byte offset of the factor block within a buffer
@@ -166,6 +165,7 @@ struct Ctx {
   bool classical;  // classical Riccati: explicit P_{n+1} in place of L_{n+1}
   bool array_qr;   // robust mode: chol(Ht + M M') by QR of [chol(Ht)'; M']
   Ring ring;
+#if GQ_IPM_TC
   // tensor-core stage products (FP32 factor of large stages)
   bool tc;            // TMEM allocated and the shape qualifies
   uint32_t taddr;     // TMEM base address (kTcCols columns)
@@ -173,7 +173,15 @@ struct Ctx {
   uint32_t tcpar;     // its next phase parity
   float* tcA;         // A tile: high part, then the low part tc_tile_bytes() later
   float* tcB;         // B tile: high part, then the low part
+#endif
 };
+
+// the tensor-core build updates the context inside the factorisation
+#if GQ_IPM_TC
+#define GQ_FCTX Ctx
+#else
+#define GQ_FCTX const Ctx
+#endif
 
 // Sum of f(i), i in [0, count), in an order fixed by `count` alone: 32-term
 // chunks are reduced by a butterfly (bitwise identical in every lane), chunk
@@ -266,26 +274,16 @@ __device__ __forceinline__ Tf* fac_global(const Batch& B, const StageDesc& s) {
   return reinterpret_cast<Tf*>(static_cast<double*>(B.fac) + s.fac);
 }
 
-// values of the general rows [D C] y of stage s (FP64, row-parallel dot
-// products with short dependent chains) into gv[ng]; block-wide, ends with a
-// barrier when ng > 0.  Every thread of the block must call it.
-__device__ __forceinline__ void general_values(const StageDesc& s, const StageData& L, const double* D,
-                                               const double* y, double* gv) {
-  const int nv = s.nx + s.nu;
-  if (s.ng > 0) {  // uniform across the block
-    rows_dot<double>(
-        s.ng, [&](int) { return 0; }, [&](int) { return nv; },
-        [&](int g, int j) { return D[L.DC + (int64_t)g * nv + j] * y[j]; }, [&](int g, double v) { gv[g] = v; });
-    __syncthreads();
-  }
-}
-
-// value of constraint c of stage s at y, general rows from general_values
+// value of constraint c of stage s at the stage vector y (length nv)
 __device__ __forceinline__ double cons_value(const StageDesc& s, const StageData& L, const double* D, int c,
-                                             const double* y, const double* gv) {
+                                             const double* y) {
   const int nb = s.nbu + s.nbx;
   if (c < nb) return y[box_idx(D, L)[c]];
-  return gv[c - nb];
+  const int nv = s.nx + s.nu;
+  const double* row = D + L.DC + (int64_t)(c - nb) * nv;
+  double v = 0.0;
+  for (int j = 0; j < nv; ++j) v = fma(row[j], y[j], v);
+  return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -299,9 +297,9 @@ __device__ __forceinline__ void ring_issue(Ctx& C, int n, int b, int fac_elem) {
     const uint32_t fbytes = fac_elem ? (uint32_t)(fac_block_elems(s.nx + s.nu) * fac_elem) : 0u;
     fence_async_shared();
     mbar_arrive_expect_tx(&C.ring.bar[b], dbytes + fbytes);
-    bulk_g2s((C.ring.buf0 + b * C.ring.slot), B.data + s.data, dbytes, &C.ring.bar[b]);
+    bulk_g2s(C.ring.buf[b], B.data + s.data, dbytes, &C.ring.bar[b]);
     if (fbytes)
-      bulk_g2s(C.ring.buf0 + b * C.ring.slot + C.ring.fac_off, static_cast<const unsigned char*>(B.fac) + s.fac * 8, fbytes,
+      bulk_g2s(C.ring.buf[b] + C.ring.fac_off, static_cast<const unsigned char*>(B.fac) + s.fac * 8, fbytes,
                &C.ring.bar[b]);
   }
 }
@@ -336,7 +334,7 @@ __device__ void sweep(Ctx& C, bool backward, int fac_elem, F f) {
     const int n = backward ? N - k : k, b = k & 1;
     if (k < N) ring_issue(C, backward ? n - 1 : n + 1, b ^ 1, fac_elem);
     ring_wait(C, b);
-    f(n, reinterpret_cast<const double*>((C.ring.buf0 + b * C.ring.slot)), static_cast<const void*>(C.ring.buf0 + b * C.ring.slot + C.ring.fac_off));
+    f(n, reinterpret_cast<const double*>(C.ring.buf[b]), static_cast<const void*>(C.ring.buf[b] + C.ring.fac_off));
     __syncthreads();
   }
 }
@@ -364,18 +362,17 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
   // r_g rows: [RSQ row | [B A]' row] . [y_n | pi_{n+1}], then the rest
   {
     const double* pn1 = pi + s.eq;
-    const int kdyn = n < C.N ? nv + nx1 : nv;  // then the ng general-row terms
+    const int kend = n < C.N ? nv + nx1 : nv;
     rows_dot<double>(
-        nv, [&](int) { return 0; }, [&](int) { return kdyn + s.ng; },
+        nv, [&](int) { return 0; }, [&](int) { return kend; },
         [&](int i, int k) {
-          if (k < nv) return D[L.RSQ + (int64_t)i * L.ldr + k] * yn[k];
-          if (k < kdyn) return D[L.BAt + (int64_t)i * L.ldb + (k - nv)] * pn1[k - nv];
-          const int g = k - kdyn;
-          return -D[L.DC + (int64_t)g * nv + i] * (lm[nb + g] - lm[nc + nb + g]);
+          return k < nv ? D[L.RSQ + (int64_t)i * L.ldr + k] * yn[k] : D[L.BAt + (int64_t)i * L.ldb + (k - nv)] * pn1[k - nv];
         },
         [&](int i, double v) {
           double acc = (lin ? add_g[s.var + i] : D[L.rq + i]) + v;
           if (n > 0 && i >= s.nu) acc -= pi[C.st[n - 1].eq + (i - s.nu)];
+          for (int g = 0; g < s.ng; ++g)
+            acc = fma(-D[L.DC + (int64_t)g * nv + i], lm[nb + g] - lm[nc + nb + g], acc);
           if (nb > 0) {
             const int c = bmap[i];
             if (c >= 0) acc -= lm[c] - lm[nc + c];
@@ -396,10 +393,8 @@ __device__ void stage_residual(const Ctx& C, int n, const double* D, const doubl
         });
   }
   if (rd != nullptr) {
-    double* gv = C.vbuf + 6 * C.vmax;
-    general_values(s, L, D, yn, gv);
     for (int c = tid; c < nc; c += NT) {
-      const double v = cons_value(s, L, D, c, yn, gv);
+      const double v = cons_value(s, L, D, c, yn);
       const double lo = D[L.lo + c], hi = D[L.hi + c];
       const int il = s.side + c, iu = s.side + nc + c;
       double a = 0.0, b = 0.0;
@@ -600,7 +595,7 @@ __device__ __noinline__ void tc_products(Ctx& C, int n, const double* D, const S
 #endif  // GQ_IPM_TC
 
 template <typename Tf>
-__device__ bool factor_stage(Ctx& C, int n, const double* D, double reg) {
+__device__ bool factor_stage(GQ_FCTX& C, int n, const double* D, double reg) {
   const Batch& B = *C.B;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int ldP = block_ld(C.nvmax);
@@ -614,13 +609,13 @@ __device__ bool factor_stage(Ctx& C, int n, const double* D, double reg) {
   const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng, nx1 = s.nx1;
   const int ne = elim_size(s, n), nk = nv - ne;
   const double* lm = B.lam + s.side;
-  const double* ti = B.tinv + s.side;
+  const double* tt = B.t + s.side;
   const int32_t* bmap = box_idx(D, L) + nb;
   // barrier weights W_lo + W_hi per constraint
   for (int c = tid; c < nc; c += NT) {
     double w = 0.0;
-    if (D[L.lo + c] != -INFINITY) w += lm[c] * ti[c];
-    if (D[L.hi + c] != INFINITY) w += lm[nc + c] * ti[nc + c];
+    if (D[L.lo + c] != -INFINITY) w += lm[c] / tt[c];
+    if (D[L.hi + c] != INFINITY) w += lm[nc + c] / tt[nc + c];
     sw[c] = (Tf)w;
   }
   if (GQ_IPM_SOFT && s.ns > 0) {
@@ -1033,12 +1028,12 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     const int32_t* bmap = box_idx(D, L) + nb;
     if (rd != nullptr) {
       const double* lm = B.lam + s.side;
-      const double* ti = B.tinv + s.side;
+      const double* tt = B.t + s.side;
       for (int c = tid; c < nc; c += NT) {
         const int il = s.side + c, iu = s.side + nc + c;
         double v = 0.0;
-        if (D[L.lo + c] != -INFINITY) v += (lm[c] * rd[il] - rm[il]) * ti[c];
-        if (D[L.hi + c] != INFINITY) v -= (lm[nc + c] * rd[iu] - rm[iu]) * ti[nc + c];
+        if (D[L.lo + c] != -INFINITY) v += (lm[c] * rd[il] - rm[il]) / tt[c];
+        if (D[L.hi + c] != INFINITY) v -= (lm[nc + c] * rd[iu] - rm[iu]) / tt[nc + c];
         vs[c] = v;
       }
       if (GQ_IPM_SOFT && s.ns > 0) {
@@ -1061,15 +1056,6 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
           [&](int k, int j) { return sL[j * nx1 + k] * (Tf)rb[s.eq + j]; }, [&](int k, Tf v) { va[k] = v; });
     }
     __syncthreads();
-    // general rows' part of the reduced gradient, [D C]' v_g (FP64, row-parallel)
-    double* gtv = C.vbuf + 7 * C.vmax;
-    const bool gen = rd != nullptr && s.ng > 0;
-    if (gen) {
-      rows_dot<double>(
-          nv, [&](int) { return 0; }, [&](int) { return s.ng; },
-          [&](int i, int gg) { return D[L.DC + (int64_t)gg * nv + i] * vs[nb + gg]; },
-          [&](int i, double v) { gtv[i] = v; });
-    }
     if (n < C.N) {
       if (C.classical) {
         // vb = P_{n+1} rb_n + p_{n+1}
@@ -1093,7 +1079,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
           [&](int i, Tf v) {
             double gi = g[s.var + i];
             if (rd != nullptr) {
-              if (gen) gi -= gtv[i];
+              for (int gg = 0; gg < s.ng; ++gg) gi = fma(-D[L.DC + (int64_t)gg * nv + i], vs[nb + gg], gi);
               if (nb > 0 && bmap[i] >= 0) gi -= vs[bmap[i]];
             }
             scale = max_nan(scale, fabs(gi));
@@ -1177,17 +1163,15 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
           [&](int k, Tf v) { x1[k] = (double)((Tf)rb[s.eq + k] + v); });
     }
     // dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt) on active sides
-    double* gv = C.vbuf + 6 * C.vmax;
-    general_values(s, L, D, yn, gv);
     for (int c = tid; c < nc; c += NT) {
-      const double v = cons_value(s, L, D, c, yn, gv);
+      const double v = cons_value(s, L, D, c, yn);
       const int il = s.side + c, iu = s.side + nc + c;
       const double dl = rd ? rd[il] : 0.0, du = rd ? rd[iu] : 0.0;
       const double ml = rm ? rm[il] : 0.0, mu = rm ? rm[iu] : 0.0;
       if (D[L.lo + c] != -INFINITY) {
         const double a = v - dl;
         dt[il] = a;
-        dlam[il] = -(ml + B.lam[il] * a) * B.tinv[il];
+        dlam[il] = -(ml + B.lam[il] * a) / B.t[il];
       } else {
         dt[il] = 0.0;
         dlam[il] = 0.0;
@@ -1195,7 +1179,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
       if (D[L.hi + c] != INFINITY) {
         const double a = -v - du;
         dt[iu] = a;
-        dlam[iu] = -(mu + B.lam[iu] * a) * B.tinv[iu];
+        dlam[iu] = -(mu + B.lam[iu] * a) / B.t[iu];
       } else {
         dt[iu] = 0.0;
         dlam[iu] = 0.0;
@@ -1340,8 +1324,8 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
   C.nvmax = sh.nvmax;
   C.nxmax = sh.nxmax;
   C.panel = smem + P.panel;
-  C.ring.buf0 = smem + P.ring0;
-  C.ring.slot = (uint32_t)(P.ring1 - P.ring0);
+  C.ring.buf[0] = smem + P.ring0;
+  C.ring.buf[1] = smem + P.ring1;
   C.ring.bar = bars;
   C.ring.parity = 0;
   C.ring.fac_off = (uint32_t)P.ring_fac;
@@ -1351,11 +1335,11 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
   C.ring.ok = true;
   // tensor-core products for large stages in the FP32 factor: one TMEM
   // allocation per block
-  C.tc = GQ_IPM_TC && tc_shape(sh) && arg.precision == GQ_PREC_MIXED && blockDim.x == 256 &&
+#if GQ_IPM_TC
+  C.tc = tc_shape(sh) && arg.precision == GQ_PREC_MIXED && blockDim.x == 256 &&
          kind != (int)LaunchKind::Residuals;
   C.tcpar = 0;
   C.taddr = 0;
-#if GQ_IPM_TC
   if (C.tc) {
     C.tcbar = reinterpret_cast<uint64_t*>(smem + P.tcbar);
     C.tcA = reinterpret_cast<float*>(smem + P.tc);
@@ -1406,10 +1390,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
 
   if (kind == (int)LaunchKind::NewtonStep) {
     residuals(C);
-    for_sides(C, [&](int i) {
-      B.rm[i] = B.lam[i] * B.t[i] - (B.lam[i] != 0.0 ? sigma_mu : 0.0);
-      B.tinv[i] = 1.0 / B.t[i];
-    });
+    for_sides(C, [&](int i) { B.rm[i] = B.lam[i] * B.t[i] - (B.lam[i] != 0.0 ? sigma_mu : 0.0); });
     __syncthreads();
     Dir d{out.dy, out.dpi, out.dlam, out.dt};
     Count cnt;
@@ -1448,10 +1429,8 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
       const StageDesc s = sst[n];
       const StageData L = lay(s);
       const int nb = s.nbu + s.nbx, nc = nb + s.ng, nv = s.nx + s.nu;
-      double* gv = C.vbuf + 6 * C.vmax;
-      general_values(s, L, D, B.y + s.var, gv);
       for (int c = tid; c < nc; c += blockDim.x) {
-        const double v = cons_value(s, L, D, c, B.y + s.var, gv);
+        const double v = cons_value(s, L, D, c, B.y + s.var);
         const double lo = D[L.lo + c], hi = D[L.hi + c];
         const int il = s.side + c, iu = s.side + nc + c;
         double sl = 0.0, su = 0.0;  // slacks of a relaxed constraint (Sec. 2.2)
@@ -1545,10 +1524,7 @@ __global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch 
       }
     }
     // a2 + a3: predictor right-hand side and factorisation
-    for_sides(C, [&](int i) {
-      B.rm[i] = B.lam[i] * B.t[i];
-      B.tinv[i] = 1.0 / B.t[i];  // one division per side and iteration
-    });
+    for_sides(C, [&](int i) { B.rm[i] = B.lam[i] * B.t[i]; });
     __syncthreads();
     const double reg = fp64 ? (mixed ? 0.0 : arg.reg_prim) : arg.reg_prim;
     bool ok = fp64 ? factor<double>(C, reg) : factor<float>(C, reg);

@@ -99,11 +99,13 @@ def test_large_stage_full_batch(env, precision):
 
 def test_large_stage_with_and_without_tensor_cores(env):
     """The same large-stage QPs (nu + nx = 192) in the mixed path with the
-    tcgen05 products (schedule tensor_cores = 1) and with the warp-level
-    mma.sync products (0): both meet the oracle gates."""
+    tcgen05 products (schedule tensor_cores = 2, and 1 = automatic, which
+    takes them for two QPs on a GPU of at least four SMs) and with the
+    warp-level mma.sync products (0):
+    all meet the oracle gates."""
     gq, QpBatch, torch = env
     qps = [W.large_stage_qp(i, N=6) for i in range(2)]
-    for tc in (1, 0):
+    for tc in (2, 1, 0):
         b = QpBatch(qps)
         b.set_schedule(32, 256, tc)
         assert b.schedule().tensor_cores == tc

@@ -365,7 +365,7 @@ def test_schedules_agree_and_autotune_picks_one(env):
         b.upload()
         sch, ms = b.autotune(arg, reps=2)
         assert sch.warp_max_nv in (32, 24, 16, 0) and sch.block_threads in (256, 128, 64) and ms > 0
-        assert sch.tensor_cores in (0, 1)
+        assert sch.tensor_cores in (0, 2)
         b.solve(arg)
         b.download()
         torch.cuda.synchronize()
