@@ -539,7 +539,9 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
   const Batch& B = *C.B;
   const int lane = C.lane;
   T* sL = static_cast<T*>(C.sL);
-  double* lp = B.lp;
+  // l and p of each stage, from the backward sweep to the forward one, kept
+  // in the factor's precision (the FP64 workspace vector holds them)
+  T* lp = reinterpret_cast<T*>(B.lp);
   const void* dbase = sizeof(T) == 8 ? static_cast<const void*>(B.data) : static_cast<const void*>(B.data32);
   double scale = 0.0;
   T p1 = T(0);  // p_{n+1}, element `lane`
@@ -559,8 +561,8 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
         if (c < nc) {
           const int il = s.side + c, iu = s.side + nc + c;
           double v = 0.0;
-          if ((double)D[L.lo + c] != -INFINITY) v += (B.lam[il] * rd[il] - rm[il]) * B.tinv[il];
-          if ((double)D[L.hi + c] != INFINITY) v -= (B.lam[iu] * rd[iu] - rm[iu]) * B.tinv[iu];
+          if (D[L.lo + c] != (T)-INFINITY) v += (B.lam[il] * rd[il] - rm[il]) * B.tinv[il];
+          if (D[L.hi + c] != (T)INFINITY) v -= (B.lam[iu] * rd[iu] - rm[iu]) * B.tinv[iu];
           C.sv[c] = v;
         }
       }
@@ -629,8 +631,8 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
       #pragma unroll 4
       for (int j = 0; j < ne; ++j) p -= lr[j] * lv[j];
     }
-    if (lane < ne) lp[s.var + lane] = (double)l;
-    if (lane < nk) lp[s.var + ne + lane] = (double)p;
+    if (lane < ne) lp[s.var + lane] = l;
+    if (lane < nk) lp[s.var + ne + lane] = p;
     p1 = lane < nk ? p : T(0);
     for (int a = 0; a < nk; ++a)
       if (lane < nk) sL[a * LDS + lane] = lane <= a ? F[(int64_t)(ne + a) * ldf + ne + lane] : T(0);
@@ -658,7 +660,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
         if (j >= lane && lane < nk) w += F[(int64_t)(ne + j) * ldf + ne + lane] * xv[ne + j];
       }
       const T* wv = wbcast<T>(C, 1, w);
-      T pk = lane < nk ? (T)lp[s.var + ne + lane] : T(0);
+      T pk = lane < nk ? lp[s.var + ne + lane] : T(0);
       #pragma unroll 4
       for (int j = 0; j < nk; ++j) {
         if (j <= lane && lane < nk) pk += F[(int64_t)(ne + lane) * ldf + ne + j] * wv[j];
@@ -666,7 +668,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
       if (lane < nk) dpi[C.st[n - 1].eq + lane] = (double)pk;
     }
     // va = l + L_ke' x_n (lanes < ne)
-    T va = lane < ne ? (T)lp[s.var + lane] : T(0);
+    T va = lane < ne ? lp[s.var + lane] : T(0);
     #pragma unroll 4
     for (int i = 0; i < nk; ++i) {
       if (lane < ne) va += F[(int64_t)(ne + i) * ldf + lane] * xv[ne + i];
@@ -712,7 +714,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
         const int il = s.side + c, iu = s.side + nc + c;
         const double dl = rd ? rd[il] : 0.0, du = rd ? rd[iu] : 0.0;
         const double ml = rm ? rm[il] : 0.0, mu = rm ? rm[iu] : 0.0;
-        if ((double)D[L.lo + c] != -INFINITY) {
+        if (D[L.lo + c] != (T)-INFINITY) {
           const double a = v - dl;
           dt[il] = a;
           dlam[il] = -(ml + B.lam[il] * a) * B.tinv[il];
@@ -720,7 +722,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
           dt[il] = 0.0;
           dlam[il] = 0.0;
         }
-        if ((double)D[L.hi + c] != INFINITY) {
+        if (D[L.hi + c] != (T)INFINITY) {
           const double a = -v - du;
           dt[iu] = a;
           dlam[iu] = -(mu + B.lam[iu] * a) * B.tinv[iu];
@@ -778,15 +780,34 @@ __device__ double wnewton(WCtx& C, const WDir& d, int ir, double ir_tol, WCount*
   return ratio;
 }
 
+// largest step to the boundary: the minimum over sides of lambda / -dlambda
+// and t / -dt where the direction decreases them.  Each lane keeps its
+// running minimum as a fraction num / den (den > 0 once set; 1 / 0 = +inf
+// stands for no blocking side) and compares candidates by cross-
+// multiplication, so it divides once, for its own winner, instead of once
+// per side (an FP64 division is a long sequence on the FP64 pipe).
 __device__ double wmax_step(const WCtx& C, const double* dlam, const double* dt) {
   const Batch& B = *C.B;
-  double a = INFINITY;
+  double num = 1.0, den = 0.0;
   #pragma unroll 4
   for (int i = C.side0 + C.lane; i < C.side0 + C.nside; i += 32) {
-    if (dlam[i] < 0.0) a = fmin(a, -B.lam[i] / dlam[i]);
-    if (dt[i] < 0.0) a = fmin(a, -B.t[i] / dt[i]);
+    const double dl = dlam[i], dd = dt[i];
+    if (dl < 0.0) {
+      const double a = B.lam[i];
+      if (a * den < num * -dl) {
+        num = a;
+        den = -dl;
+      }
+    }
+    if (dd < 0.0) {
+      const double a = B.t[i];
+      if (a * den < num * -dd) {
+        num = a;
+        den = -dd;
+      }
+    }
   }
-  return warp_min(a);
+  return warp_min(num / den);
 }
 
 __device__ double wmu_after(const WCtx& C, double alpha, const double* dlam, const double* dt) {
@@ -1031,8 +1052,12 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
       }
     }
     #pragma unroll 4
-    for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) B.rm[i] = B.lam[i] * B.t[i];
-    set_tinv();
+    for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) {
+      const double ti = B.t[i];
+      B.rm[i] = B.lam[i] * ti;
+      B.tinv[i] = 1.0 / ti;
+    }
+    __syncwarp();
     const double reg = fp64 ? (mixed ? 0.0 : arg.reg_prim) : arg.reg_prim;
     bool ok = wfactor<T>(C, reg);
     ++cnt.fact;
@@ -1088,8 +1113,10 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
         B.rm[i] = B.lam[i] != 0.0 ? B.lam[i] * B.t[i] + d.dlam[i] * d.dt[i] - smu : 0.0;
       __syncwarp();
       double ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
+      double amax = -1.0;  // step to the boundary of the current direction, once known
       if (arg.cond_corr) {
-        const double a_c = fmin(1.0, wmax_step(C, d.dlam, d.dt));
+        amax = wmax_step(C, d.dlam, d.dt);
+        const double a_c = fmin(1.0, amax);
         const double mu_c = wmu_after(C, a_c, d.dlam, d.dt);
         if (mu_c > arg.corr_k * mu_aff) {
           #pragma unroll 4
@@ -1097,6 +1124,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
             B.rm[i] = B.lam[i] != 0.0 ? B.lam[i] * B.t[i] - smu : 0.0;
           __syncwarp();
           ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
+          amax = -1.0;
         }
       }
       if (ir > 0 && !(ratio <= arg.ir_fail_ratio && cnt.m <= inexact)) {
@@ -1113,7 +1141,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
           continue;
         }
       }
-      alpha = fmin(1.0, arg.tau_b * wmax_step(C, d.dlam, d.dt));
+      alpha = fmin(1.0, arg.tau_b * (amax >= 0.0 ? amax : wmax_step(C, d.dlam, d.dt)));
     } else {
       if (ir > 0) {
         const double ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
