@@ -158,6 +158,17 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
   const double yl = lane < nv ? y[s.var + lane] : 0.0;
   const double pl = (n < C.N && lane < nx1) ? pi[s.eq + lane] : 0.0;
   const double* lm = lam + s.side;
+  // the other global terms of rows r_g and r_b, loaded before the mat-vecs
+  // (their loads would otherwise wait behind the broadcast barriers)
+  const double g0 = lane < nv ? (lin ? add_g[s.var + lane] : D[L.rq + lane]) : 0.0;
+  const double pprev = (n > 0 && lane >= s.nu && lane < nv) ? pi[C.st[n - 1].eq + (lane - s.nu)] : 0.0;
+  const int cbox = (nb > 0 && lane < nv) ? bmap[lane] : -1;
+  const double lbox = cbox >= 0 ? lm[cbox] - lm[nc + cbox] : 0.0;
+  const bool brow = n < C.N && lane < nx1;
+  const double b0 = brow ? (lin ? add_b[s.eq + lane] : D[L.b + lane]) : 0.0;
+  const double x1 = brow ? y[C.st[n + 1].var + C.st[n + 1].nu + lane] : 0.0;
+  const bool side0 = rd != nullptr && lane < nc;
+  const double tl0 = side0 ? t[s.side + lane] : 0.0, tu0 = side0 ? t[s.side + nc + lane] : 0.0;
   const double* yv = wbcast<double>(C, 0, yl);
   // r_g, row `lane`
   {
@@ -182,13 +193,10 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
       if (k < nx1) a0 = fma(ba[k], pv[k], a0);
     }
     if (lane < nv) {
-      double acc = (lin ? add_g[s.var + lane] : D[L.rq + lane]) + (a0 + a1);
-      if (n > 0 && lane >= s.nu) acc -= pi[C.st[n - 1].eq + (lane - s.nu)];
+      double acc = g0 + (a0 + a1);
+      if (n > 0 && lane >= s.nu) acc -= pprev;
       for (int g = 0; g < s.ng; ++g) acc = fma(-D[L.DC + (int64_t)g * nv + lane], lm[nb + g] - lm[nc + nb + g], acc);
-      if (nb > 0) {
-        const int c = bmap[lane];
-        if (c >= 0) acc -= lm[c] - lm[nc + c];
-      }
+      if (cbox >= 0) acc -= lbox;
       og[s.var + lane] = acc;
       mx.g = max_nan(mx.g, fabs(acc));
     }
@@ -205,8 +213,7 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
     }
     if (i < nv) a0 = fma(D[L.BAt + (int64_t)i * L.ldb + kk], yv[i], a0);
     if (lane < nx1) {
-      const double x1 = y[C.st[n + 1].var + C.st[n + 1].nu + lane];
-      const double acc = (lin ? add_b[s.eq + lane] : D[L.b + lane]) + (a0 + a1) - x1;
+      const double acc = b0 + (a0 + a1) - x1;
       ob[s.eq + lane] = acc;
       mx.b = max_nan(mx.b, fabs(acc));
     }
@@ -227,8 +234,8 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
         const double lo = D[L.lo + c], hi = D[L.hi + c];
         const int il = s.side + c, iu = s.side + nc + c;
         double a = 0.0, bb = 0.0;
-        if (lo != -INFINITY) a = lo - v + t[il];
-        if (hi != INFINITY) bb = v - hi + t[iu];
+        if (lo != -INFINITY) a = lo - v + (c0 == 0 ? tl0 : t[il]);
+        if (hi != INFINITY) bb = v - hi + (c0 == 0 ? tu0 : t[iu]);
         rd[il] = a;
         rd[iu] = bb;
         mx.d = max_nan(mx.d, max_nan(fabs(a), fabs(bb)));
@@ -295,13 +302,15 @@ __device__ __forceinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double
   const int32_t* bmap = reinterpret_cast<const int32_t*>(D + L.box) + nb;
   const bool act = lane < nv;
   const int i = act ? lane : 0;
-  // barrier weights W_lo + W_hi per constraint
-  for (int c = lane; c < nc; c += 32) {
+  // barrier weights W_lo + W_hi per constraint; the first 32 are loaded here
+  // and stored after the products, so that their global loads overlap them
+  auto weight = [&](int c) {
     double w = 0.0;
     if (D[L.lo + c] != -INFINITY) w += B.lam[s.side + c] * B.tinv[s.side + c];
     if (D[L.hi + c] != INFINITY) w += B.lam[s.side + nc + c] * B.tinv[s.side + nc + c];
-    sw[c] = (T)w;
-  }
+    return w;
+  };
+  const double w0 = lane < nc ? weight(lane) : 0.0;
   constexpr bool kMma = sizeof(T) == 4;
   // M row i: M[i][j] = sum_{k >= j} [B A]'[i][k] L_{n+1}[k][j]
   if constexpr (kMma) {
@@ -351,6 +360,8 @@ __device__ __forceinline__ bool wfactor_stage(WCtx& C, int n, const T* D, double
       sM[i * LDS + j] = (a0 + a1) + (a2 + a3);
     }
   }
+  if (lane < nc) sw[lane] = (T)w0;
+  for (int c = lane + 32; c < nc; c += 32) sw[c] = (T)weight(c);
   __syncwarp();
   // Phi row i (lower part): RSQ + M M' + [D C]' diag(w_g) [D C] + diagonal terms
   if constexpr (kMma) {
@@ -554,6 +565,9 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
     const int ne = welim(s, n), nk = nv - ne;
     const int ldf = odd_ld(nv);
     const int32_t* bmap = reinterpret_cast<const int32_t*>(D + L.box) + nb;
+    // global loads of this stage's rows, issued before the per-side pass
+    const double g0 = lane < nv ? g[s.var + lane] : 0.0;
+    const double rb0 = (n < C.N && lane < nx1) ? rb[s.eq + lane] : 0.0;
     // per-constraint v_lo - v_hi, v = (lambda r_d - r_m) / t
     if (rd != nullptr) {
       for (int c0 = 0; c0 < nc; c0 += 32) {
@@ -571,7 +585,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
     // reduced gradient element `lane`
     double gi = 0.0;
     if (lane < nv) {
-      gi = g[s.var + lane];
+      gi = g0;
       if (rd != nullptr) {
         for (int gg = 0; gg < s.ng; ++gg) gi = fma(-(double)D[L.DC + (int64_t)gg * nv + lane], C.sv[nb + gg], gi);
         if (nb > 0 && bmap[lane] >= 0) gi -= C.sv[bmap[lane]];
@@ -580,7 +594,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
     }
     T vb = T(0);
     if (n < C.N) {
-      const double rbd = lane < nx1 ? rb[s.eq + lane] : 0.0;
+      const double rbd = rb0;
       scale = max_nan(scale, fabs(rbd));
       const T rbl = (T)rbd;
       // va = L_{n+1}' rb
@@ -638,7 +652,9 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
       if (lane < nk) sL[a * LDS + lane] = lane <= a ? F[(int64_t)(ne + a) * ldf + ne + lane] : T(0);
     __syncwarp();
   });
-  // forward sweep
+  // forward sweep; x_{n+1} passes to the next stage in a register (lane k
+  // holds element k), besides its store into dy
+  T xn = T(0);
   wsweep(C, false, dbase, (int)sizeof(T), B.fac, (int)sizeof(T), [&](int n, const void* Dv, const void* Fv) {
     const T* D = static_cast<const T*>(Dv);
     const T* F = static_cast<const T*>(Fv);
@@ -648,8 +664,21 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
     const int ne = welim(s, n), nk = nv - ne;
     const int ldf = odd_ld(nv);
     const int32_t* bidx = reinterpret_cast<const int32_t*>(D + L.box);
-    // x_n (lanes ne..nv-1 of the stage vector), written by the previous stage
-    const double xd = (lane >= ne && lane < nv) ? dy[s.var + lane] : 0.0;
+    // global loads of this stage, issued before the recursion's dependent
+    // steps: l and p of the backward sweep, rb, and the per-side terms of the
+    // recovery for the first 32 constraints
+    const T lpk = (n > 0 && lane < nk) ? lp[s.var + ne + lane] : T(0);
+    const T lpe = lane < ne ? lp[s.var + lane] : T(0);
+    const T rbn = (n < C.N && lane < nx1) ? (T)rb[s.eq + lane] : T(0);
+    const int c0l = lane, il0 = s.side + c0l, iu0 = s.side + nc + c0l;
+    const bool side0 = lane < nc;
+    const double dl0 = (side0 && rd) ? rd[il0] : 0.0, du0 = (side0 && rd) ? rd[iu0] : 0.0;
+    const double ml0 = (side0 && rm) ? rm[il0] : 0.0, mu0 = (side0 && rm) ? rm[iu0] : 0.0;
+    const double la0 = side0 ? B.lam[il0] : 0.0, lb0 = side0 ? B.lam[iu0] : 0.0;
+    const double ta0 = side0 ? B.tinv[il0] : 0.0, tb0 = side0 ? B.tinv[iu0] : 0.0;
+    // x_n (lanes ne..nv-1 of the stage vector), from the previous stage
+    const T xsh = __shfl_sync(kFull, xn, (lane - ne) & 31);
+    const double xd = (lane >= ne && lane < nv) ? (double)xsh : 0.0;
     const T xl = (T)xd;
     const T* xv = wbcast<T>(C, 0, xl);
     if (n > 0) {
@@ -660,7 +689,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
         if (j >= lane && lane < nk) w += F[(int64_t)(ne + j) * ldf + ne + lane] * xv[ne + j];
       }
       const T* wv = wbcast<T>(C, 1, w);
-      T pk = lane < nk ? lp[s.var + ne + lane] : T(0);
+      T pk = lpk;
       #pragma unroll 4
       for (int j = 0; j < nk; ++j) {
         if (j <= lane && lane < nk) pk += F[(int64_t)(ne + lane) * ldf + ne + j] * wv[j];
@@ -668,7 +697,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
       if (lane < nk) dpi[C.st[n - 1].eq + lane] = (double)pk;
     }
     // va = l + L_ke' x_n (lanes < ne)
-    T va = lane < ne ? lp[s.var + lane] : T(0);
+    T va = lpe;
     #pragma unroll 4
     for (int i = 0; i < nk; ++i) {
       if (lane < ne) va += F[(int64_t)(ne + i) * ldf + lane] * xv[ne + i];
@@ -686,7 +715,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
     if (n < C.N) {
       // x_{n+1} = [B A] y_n + rb_n
       const T* yv = wbcast<T>(C, 0, yl);
-      T acc = lane < nx1 ? (T)rb[s.eq + lane] : T(0);
+      T acc = rbn;
       const int kk = lane < nx1 ? lane : 0;
       T acc2 = T(0);
       int i = 0;
@@ -698,6 +727,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
       if (i < nv) acc += D[L.BAt + (int64_t)i * L.ldb + kk] * yv[i];
       acc += acc2;
       if (lane < nx1) dy[C.st[n + 1].var + C.st[n + 1].nu + lane] = (double)acc;
+      xn = acc;
     }
     // dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt), FP64
     for (int gg = 0; gg < s.ng; ++gg) {
@@ -712,12 +742,13 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
       if (c < nc) {
         const double v = c < nb ? yb : C.sv[c - nb];
         const int il = s.side + c, iu = s.side + nc + c;
-        const double dl = rd ? rd[il] : 0.0, du = rd ? rd[iu] : 0.0;
-        const double ml = rm ? rm[il] : 0.0, mu = rm ? rm[iu] : 0.0;
+        const bool first = c0 == 0;
+        const double dl = first ? dl0 : (rd ? rd[il] : 0.0), du = first ? du0 : (rd ? rd[iu] : 0.0);
+        const double ml = first ? ml0 : (rm ? rm[il] : 0.0), mu = first ? mu0 : (rm ? rm[iu] : 0.0);
         if (D[L.lo + c] != (T)-INFINITY) {
           const double a = v - dl;
           dt[il] = a;
-          dlam[il] = -(ml + B.lam[il] * a) * B.tinv[il];
+          dlam[il] = -(ml + (first ? la0 : B.lam[il]) * a) * (first ? ta0 : B.tinv[il]);
         } else {
           dt[il] = 0.0;
           dlam[il] = 0.0;
@@ -725,7 +756,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
         if (D[L.hi + c] != (T)INFINITY) {
           const double a = -v - du;
           dt[iu] = a;
-          dlam[iu] = -(mu + B.lam[iu] * a) * B.tinv[iu];
+          dlam[iu] = -(mu + (first ? lb0 : B.lam[iu]) * a) * (first ? tb0 : B.tinv[iu]);
         } else {
           dt[iu] = 0.0;
           dlam[iu] = 0.0;
