@@ -418,6 +418,8 @@ int gq_batch_create_soft(int nqp, const int* dims, size_t dims_len, const int* s
   o = align_up(o + fac * 8, 256);
   L.data32 = o;
   o = align_up(o + data * 4, 256);
+  L.data32lo = o;
+  o = align_up(o + data * 4, 256);
   L.matg = o;
   o = align_up(o + matg_elems * 8, 256);
   L.queue = o;
@@ -873,6 +875,7 @@ static int make_kernel_batch_on(const gq_batch* b, void* dev_in, void* dev_sol, 
   k->nslots = (int32_t)b->n_slots;
   k->data = reinterpret_cast<const double*>(in + L.data);
   k->data32 = reinterpret_cast<float*>(ws + L.data32);
+  k->data32lo = reinterpret_cast<float*>(ws + L.data32lo);
   k->stats = reinterpret_cast<gq_stats*>(so + L.stats);
   k->y = reinterpret_cast<double*>(so + L.y);
   k->pi = reinterpret_cast<double*>(so + L.pi);

@@ -98,7 +98,8 @@ struct Layout {
   // "sol" buffer
   int64_t stats, y, pi, lam, t, sol_bytes;
   // workspace: FP64 vectors then the factor arena
-  int64_t rg, rb, rd, rm, dy, dpi, dlam, dt, lp, rg2, rb2, dy2, dpi2, dlam2, dt2, tinv, fac, data32, matg, queue, ws_bytes;
+  int64_t rg, rb, rd, rm, dy, dpi, dlam, dt, lp, rg2, rb2, dy2, dpi2, dlam2, dt2, tinv, fac, data32, data32lo, matg, queue,
+      ws_bytes;
 };
 
 // Kernel launch parameters (passed by value).
@@ -117,6 +118,7 @@ struct Batch {
   void* fac;
   double* matg;           // per-QP stage-matrix scratch of the block kernel (global mode only)
   int32_t* queue;         // work-queue counters of the persistent launches (kQueue* slots)
+  float* data32lo;        // FP32 remainder of `data`: data = data32 + data32lo to about 48 bits
 };
 
 // slots of Batch::queue: next QP index of each persistent launch of a solve

@@ -94,6 +94,64 @@ __device__ __forceinline__ double side_sum(const WCtx& C, F f) {
   return warp_sum(acc);
 }
 
+// largest of m (not negative) and |v| by the bit patterns on the integer pipe
+// (for non-negative doubles the integer order is the numeric one, and a NaN
+// orders above every number, so it propagates as in max_nan)
+__device__ __forceinline__ double max_abs_bits(double m, double v) {
+  const long long a = __double_as_longlong(m), b = __double_as_longlong(v) & 0x7fffffffffffffffLL;
+  return __longlong_as_double(a > b ? a : b);
+}
+
+// bound tests on the integer pipe: lo is not -inf, hi is not +inf
+__device__ __forceinline__ bool lo_on(double lo) { return __double_as_longlong(lo) != (long long)0xfff0000000000000ULL; }
+__device__ __forceinline__ bool hi_on(double hi) { return __double_as_longlong(hi) != 0x7ff0000000000000LL; }
+// x != 0 (either zero) on the integer pipe; NaN counts as non-zero, as in
+// the FP64 test
+__device__ __forceinline__ bool nonzero_bits(double x) { return (__double_as_longlong(x) << 1) != 0; }
+// fmax(x, m) for m > 0 on the integer pipe: negative x (sign bit set, an
+// integer below m's) and NaN give m, as fmax does
+__device__ __forceinline__ double fmax_pos_bits(double x, double m) {
+  const long long xi = __double_as_longlong(x), mi = __double_as_longlong(m);
+  return (xi > mi && xi <= 0x7ff0000000000000LL) ? x : m;
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic on the FP32 pipe: a value carried as the unevaluated
+// sum h + l of two FP32 numbers, about 48 significant bits (Dekker's pair
+// arithmetic: the product's error by one FMA, the sum's error by Knuth's
+// two-sum).  On GB300 every FP64 instruction -- FMA, add, compare or a
+// conversion to or from FP64 -- holds a sub-partition's FP64 pipe for about
+// 70 cycles, an FP32 FMA for about 1.5, so the mixed path's refinement
+// residual, whose mat-vecs need more than FP32 but not all of FP64, takes
+// them here.  The _rn intrinsics keep the compiler from contracting the
+// error-free steps into FMAs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_split(double x, float& h, float& l) {
+  h = (float)x;
+  l = (float)(x - (double)h);
+}
+// (sh, sl) += (ah + al)(xh + xl): the product to about 2^-46 (al xl dropped),
+// the sum's rounding error and the product's low part gathered in sl
+// (renormalised once, at the end)
+__device__ __forceinline__ void df_acc(float ah, float al, float xh, float xl, float& sh, float& sl) {
+  const float p = __fmul_rn(ah, xh);
+  float e = __fmaf_rn(ah, xh, -p);
+  e = __fmaf_rn(ah, xl, e);
+  e = __fmaf_rn(al, xh, e);
+  const float t = __fadd_rn(sh, p);
+  const float bp = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+// (h0 + l0) + (h1 + l1) as a double
+__device__ __forceinline__ double df_join(float h0, float l0, float h1, float l1) {
+  const float t = __fadd_rn(h0, h1);
+  const float bp = __fsub_rn(t, h0);
+  const float err = __fadd_rn(__fsub_rn(h0, __fsub_rn(t, bp)), __fsub_rn(h1, bp));
+  return (double)t + (double)__fadd_rn(__fadd_rn(l0, l1), err);
+}
+
 // ---------------------------------------------------------------------------
 // stage sweep over the bulk-copy ring
 // ---------------------------------------------------------------------------
@@ -125,6 +183,36 @@ __device__ void wsweep(WCtx& C, bool backward, const void* dbase, int delem, con
     C.parity ^= 1u << b;
     C.ok = C.ok && ok;
     f(n, static_cast<const void*>((C.ring0 + b * C.slot)), static_cast<const void*>(C.ring0 + b * C.slot + C.fac_off));
+    __syncwarp();
+  }
+}
+
+// f(n, hi block, lo block) for every stage, forward: the FP32 mirror and its
+// remainder of each stage's data block, one after the other in a ring slot
+// (a slot holds an FP64 block, the same bytes)
+template <class F>
+__device__ void wsweep_df(WCtx& C, F f) {
+  const Batch& B = *C.B;
+  const int N = C.N;
+  auto issue = [&](int n, int b) {
+    const StageDesc& s = C.st[n];
+    if (C.lane == 0) {
+      const uint32_t bytes = (uint32_t)(wlay(s).size * 4);
+      fence_async_shared();
+      mbar_arrive_expect_tx(&C.bar[b], 2 * bytes);
+      bulk_g2s(C.ring0 + b * C.slot, B.data32 + s.data, bytes, &C.bar[b]);
+      bulk_g2s(C.ring0 + b * C.slot + bytes, B.data32lo + s.data, bytes, &C.bar[b]);
+    }
+  };
+  issue(0, 0);
+  for (int n = 0; n <= N; ++n) {
+    const int b = n & 1;
+    if (n < N) issue(n + 1, b ^ 1);
+    const bool ok = C.ok && mbar_wait(&C.bar[b], (C.parity >> b) & 1u);
+    C.parity ^= 1u << b;
+    C.ok = C.ok && ok;
+    const float* hi = reinterpret_cast<const float*>(C.ring0 + b * C.slot);
+    f(n, hi, hi + wlay(C.st[n]).size);
     __syncwarp();
   }
 }
@@ -198,7 +286,7 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
       for (int g = 0; g < s.ng; ++g) acc = fma(-D[L.DC + (int64_t)g * nv + lane], lm[nb + g] - lm[nc + nb + g], acc);
       if (cbox >= 0) acc -= lbox;
       og[s.var + lane] = acc;
-      mx.g = max_nan(mx.g, fabs(acc));
+      mx.g = max_abs_bits(mx.g, acc);
     }
   }
   // r_b, row `lane`
@@ -215,7 +303,7 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
     if (lane < nx1) {
       const double acc = b0 + (a0 + a1) - x1;
       ob[s.eq + lane] = acc;
-      mx.b = max_nan(mx.b, fabs(acc));
+      mx.b = max_abs_bits(mx.b, acc);
     }
   }
   // r_d per side
@@ -234,11 +322,11 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
         const double lo = D[L.lo + c], hi = D[L.hi + c];
         const int il = s.side + c, iu = s.side + nc + c;
         double a = 0.0, bb = 0.0;
-        if (lo != -INFINITY) a = lo - v + (c0 == 0 ? tl0 : t[il]);
-        if (hi != INFINITY) bb = v - hi + (c0 == 0 ? tu0 : t[iu]);
+        if (lo_on(lo)) a = lo - v + (c0 == 0 ? tl0 : t[il]);
+        if (hi_on(hi)) bb = v - hi + (c0 == 0 ? tu0 : t[iu]);
         rd[il] = a;
         rd[iu] = bb;
-        mx.d = max_nan(mx.d, max_nan(fabs(a), fabs(bb)));
+        mx.d = max_abs_bits(max_abs_bits(mx.d, a), bb);
       }
     }
     __syncwarp();
@@ -246,17 +334,176 @@ __device__ __forceinline__ void wres_stage(WCtx& C, int n, const double* D, cons
   (void)B;
 }
 
+// sum over lanes < nv of (Dh + Dl)[k0 + lane] (yh + ylo) in double-float, by
+// a butterfly whose two-sum errors are exact, so every lane ends with the
+// same bits
+__device__ __forceinline__ double gen_value_df(const float* Dh, const float* Dl, int64_t k0, int nv, int lane,
+                                               float yh, float ylo) {
+  float h = 0.0f, l = 0.0f;
+  if (lane < nv) {
+    const float ah = Dh[k0 + lane], al = Dl[k0 + lane];
+    h = __fmul_rn(ah, yh);
+    l = __fmaf_rn(ah, yh, -h);
+    l = __fmaf_rn(ah, ylo, l);
+    l = __fmaf_rn(al, yh, l);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(kFull, h, o), l2 = __shfl_xor_sync(kFull, l, o);
+    const float t = __fadd_rn(h, h2);
+    const float bp = __fsub_rn(t, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(t, bp)), __fsub_rn(h2, bp));
+    h = t;
+    l = __fadd_rn(__fadd_rn(l, l2), err);
+  }
+  return (double)h + (double)l;
+}
+
+// the residuals of eq. (delta) for one stage (wres_stage) with the mat-vecs
+// in double-float from the FP32 data mirror and its remainder, two
+// independent chains per row; the other terms in FP64.  kFull: the iterate's
+// residual, r_d included (the linear terms, bounds and general rows read
+// from the FP64 data block in global memory); else the refinement residual
+// of a direction (r_g and r_b rows, add_g and add_b in place of q and b).
+template <bool kFull>
+__device__ __forceinline__ void wres_stage_df(WCtx& C, int n, const float* Dh, const float* Dl, const double* y,
+                                              const double* pi, const double* lam, const double* t, double* og,
+                                              double* ob, double* rd, const double* add_g, const double* add_b,
+                                              WMax& mx) {
+  const int lane = C.lane;
+  const StageDesc s = C.st[n];
+  const StageData L = wlay(s);
+  const int nv = s.nx + s.nu, nb = s.nbu + s.nbx, nc = nb + s.ng, nx1 = s.nx1;
+  const int32_t* bidx = reinterpret_cast<const int32_t*>(Dh + L.box);
+  const int32_t* bmap = bidx + nb;
+  const double* D64 = C.B->data + s.data;
+  const double* lm = lam + s.side;
+  // global loads of the stage, issued before the mat-vecs
+  const double yl = lane < nv ? y[s.var + lane] : 0.0;
+  const double pl = (n < C.N && lane < nx1) ? pi[s.eq + lane] : 0.0;
+  const double g0 = lane < nv ? (kFull ? D64[L.rq + lane] : add_g[s.var + lane]) : 0.0;
+  const double pprev = (n > 0 && lane >= s.nu && lane < nv) ? pi[C.st[n - 1].eq + (lane - s.nu)] : 0.0;
+  const int cbox = (nb > 0 && lane < nv) ? bmap[lane] : -1;
+  const double lbox = cbox >= 0 ? lm[cbox] - lm[nc + cbox] : 0.0;
+  const bool brow = n < C.N && lane < nx1;
+  const double b0 = brow ? (kFull ? D64[L.b + lane] : add_b[s.eq + lane]) : 0.0;
+  const double x1 = brow ? y[C.st[n + 1].var + C.st[n + 1].nu + lane] : 0.0;
+  const bool side0 = kFull && lane < nc;
+  const double tl0 = side0 ? t[s.side + lane] : 0.0, tu0 = side0 ? t[s.side + nc + lane] : 0.0;
+  const double lo0 = side0 ? D64[L.lo + lane] : 0.0, hi0 = side0 ? D64[L.hi + lane] : 0.0;
+  float yh, ylo, ph, plo;
+  df_split(yl, yh, ylo);
+  df_split(pl, ph, plo);
+  // y_n and pi_n, high and low parts, readable by every lane
+  float* xb = reinterpret_cast<float*>(C.xb);
+  __syncwarp();
+  xb[lane] = yh;
+  xb[32 + lane] = ylo;
+  xb[64 + lane] = ph;
+  xb[96 + lane] = plo;
+  __syncwarp();
+  // r_g, row `lane`
+  {
+    const int64_t r = lane < nv ? lane : 0;
+    const float* rh = Dh + L.RSQ + r * L.ldr;
+    const float* rl = Dl + L.RSQ + r * L.ldr;
+    float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+    int j = 0;
+#pragma unroll 2
+    for (; j + 1 < nv; j += 2) {
+      df_acc(rh[j], rl[j], xb[j], xb[32 + j], h0, l0);
+      df_acc(rh[j + 1], rl[j + 1], xb[j + 1], xb[33 + j], h1, l1);
+    }
+    if (j < nv) df_acc(rh[j], rl[j], xb[j], xb[32 + j], h0, l0);
+    if (n < C.N) {
+      const float* bh = Dh + L.BAt + r * L.ldb;
+      const float* bl = Dl + L.BAt + r * L.ldb;
+      int k = 0;
+#pragma unroll 2
+      for (; k + 1 < nx1; k += 2) {
+        df_acc(bh[k], bl[k], xb[64 + k], xb[96 + k], h0, l0);
+        df_acc(bh[k + 1], bl[k + 1], xb[65 + k], xb[97 + k], h1, l1);
+      }
+      if (k < nx1) df_acc(bh[k], bl[k], xb[64 + k], xb[96 + k], h0, l0);
+    }
+    if (lane < nv) {
+      double acc = g0 + df_join(h0, l0, h1, l1);
+      if (n > 0 && lane >= s.nu) acc -= pprev;
+      for (int g = 0; g < s.ng; ++g) acc = fma(-D64[L.DC + (int64_t)g * nv + lane], lm[nb + g] - lm[nc + nb + g], acc);
+      if (cbox >= 0) acc -= lbox;
+      og[s.var + lane] = acc;
+      mx.g = max_abs_bits(mx.g, acc);
+    }
+  }
+  // r_b, row `lane`
+  if (n < C.N) {
+    const int kk = lane < nx1 ? lane : 0;
+    float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+    int i = 0;
+#pragma unroll 2
+    for (; i + 1 < nv; i += 2) {
+      const int64_t k = L.BAt + (int64_t)i * L.ldb + kk;
+      df_acc(Dh[k], Dl[k], xb[i], xb[32 + i], h0, l0);
+      df_acc(Dh[k + L.ldb], Dl[k + L.ldb], xb[i + 1], xb[33 + i], h1, l1);
+    }
+    if (i < nv) {
+      const int64_t k = L.BAt + (int64_t)i * L.ldb + kk;
+      df_acc(Dh[k], Dl[k], xb[i], xb[32 + i], h0, l0);
+    }
+    if (lane < nx1) {
+      const double acc = b0 + df_join(h0, l0, h1, l1) - x1;
+      ob[s.eq + lane] = acc;
+      mx.b = max_abs_bits(mx.b, acc);
+    }
+  }
+  // r_d per side
+  if constexpr (kFull) {
+    for (int g = 0; g < s.ng; ++g) {
+      const double v = gen_value_df(Dh, Dl, L.DC + (int64_t)g * nv, nv, lane, yh, ylo);
+      if (lane == 0) C.sv[g] = v;
+    }
+    __syncwarp();
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+      const int c = c0 + lane;
+      const int src = (c < nb) ? bidx[c] : 0;
+      const double yb = __shfl_sync(dev::kFull, yl, src);
+      if (c < nc) {
+        const double v = c < nb ? yb : C.sv[c - nb];
+        const bool first = c0 == 0;
+        const double lo = first ? lo0 : D64[L.lo + c], hi = first ? hi0 : D64[L.hi + c];
+        const int il = s.side + c, iu = s.side + nc + c;
+        double a = 0.0, bb = 0.0;
+        if (lo_on(lo)) a = lo - v + (first ? tl0 : t[il]);
+        if (hi_on(hi)) bb = v - hi + (first ? tu0 : t[iu]);
+        rd[il] = a;
+        rd[iu] = bb;
+        mx.d = max_abs_bits(max_abs_bits(mx.d, a), bb);
+      }
+    }
+    __syncwarp();
+  }
+}
+
 struct WNorms {
   double g, b, d, mu;
 };
 
+// the iterate's residuals; with T = float (the mixed path) the mat-vecs in
+// double-float
+template <typename T>
 __device__ WNorms wresiduals(WCtx& C) {
   const Batch& B = *C.B;
   WMax mx{0.0, 0.0, 0.0};
-  wsweep(C, false, B.data, 8, nullptr, 0, [&](int n, const void* Dv, const void*) {
-    wres_stage(C, n, static_cast<const double*>(Dv), B.y, B.pi, B.lam, B.t, B.rg, B.rb, B.rd, false, nullptr,
-               nullptr, mx);
-  });
+  if constexpr (sizeof(T) == 4) {
+    wsweep_df(C, [&](int n, const float* Dh, const float* Dl) {
+      wres_stage_df<true>(C, n, Dh, Dl, B.y, B.pi, B.lam, B.t, B.rg, B.rb, B.rd, nullptr, nullptr, mx);
+    });
+  } else {
+    wsweep(C, false, B.data, 8, nullptr, 0, [&](int n, const void* Dv, const void*) {
+      wres_stage(C, n, static_cast<const double*>(Dv), B.y, B.pi, B.lam, B.t, B.rg, B.rb, B.rd, false, nullptr,
+                 nullptr, mx);
+    });
+  }
   WNorms r;
   r.g = warp_max(mx.g);
   r.b = warp_max(mx.b);
@@ -590,12 +837,12 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
         for (int gg = 0; gg < s.ng; ++gg) gi = fma(-(double)D[L.DC + (int64_t)gg * nv + lane], C.sv[nb + gg], gi);
         if (nb > 0 && bmap[lane] >= 0) gi -= C.sv[bmap[lane]];
       }
-      scale = max_nan(scale, fabs(gi));
+      scale = max_abs_bits(scale, gi);
     }
     T vb = T(0);
     if (n < C.N) {
       const double rbd = rb0;
-      scale = max_nan(scale, fabs(rbd));
+      scale = max_abs_bits(scale, rbd);
       const T rbl = (T)rbd;
       // va = L_{n+1}' rb
       const T* rbv = wbcast<T>(C, 0, rbl);
@@ -678,8 +925,9 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
     const double ta0 = side0 ? B.tinv[il0] : 0.0, tb0 = side0 ? B.tinv[iu0] : 0.0;
     // x_n (lanes ne..nv-1 of the stage vector), from the previous stage
     const T xsh = __shfl_sync(kFull, xn, (lane - ne) & 31);
-    const double xd = (lane >= ne && lane < nv) ? (double)xsh : 0.0;
-    const T xl = (T)xd;
+    const bool xlane = lane >= ne && lane < nv;
+    const double xd = xlane ? (double)xsh : 0.0;
+    const T xl = xlane ? xsh : T(0);  // (T)xd, without the conversion
     const T* xv = wbcast<T>(C, 0, xl);
     if (n > 0) {
       // pi_n = L_n (L_n' x_n) + p_n, L_n = L_kk
@@ -711,7 +959,7 @@ __device__ __forceinline__ double wsolve(WCtx& C, const double* g, const double*
     }
     const double yd = lane < ne ? (double)u : xd;
     if (lane < ne) dy[s.var + lane] = yd;
-    const T yl = (T)yd;
+    const T yl = lane < ne ? u : xl;  // (T)yd, without the conversion
     if (n < C.N) {
       // x_{n+1} = [B A] y_n + rb_n
       const T* yv = wbcast<T>(C, 0, yl);
@@ -785,10 +1033,16 @@ __device__ double wnewton(WCtx& C, const WDir& d, int ir, double ir_tol, WCount*
   double ratio = 0.0;
   for (int k = 0; k <= ir; ++k) {
     WMax mx{0.0, 0.0, 0.0};
-    wsweep(C, false, B.data, 8, nullptr, 0, [&](int n, const void* Dv, const void*) {
-      wres_stage(C, n, static_cast<const double*>(Dv), d.dy, d.dpi, d.dlam, nullptr, B.rg2, B.rb2, nullptr, true,
-                 B.rg, B.rb, mx);
-    });
+    if constexpr (sizeof(T) == 4) {
+      wsweep_df(C, [&](int n, const float* Dh, const float* Dl) {
+        wres_stage_df<false>(C, n, Dh, Dl, d.dy, d.dpi, d.dlam, nullptr, B.rg2, B.rb2, nullptr, B.rg, B.rb, mx);
+      });
+    } else {
+      wsweep(C, false, B.data, 8, nullptr, 0, [&](int n, const void* Dv, const void*) {
+        wres_stage(C, n, static_cast<const double*>(Dv), d.dy, d.dpi, d.dlam, nullptr, B.rg2, B.rb2, nullptr, true,
+                   B.rg, B.rb, mx);
+      });
+    }
     ++cnt->res;
     const double m = warp_max(max_nan(mx.g, mx.b));
     ratio = mr > 0.0 ? m / mr : 0.0;
@@ -817,20 +1071,23 @@ __device__ double wnewton(WCtx& C, const WDir& d, int ir, double ir_tol, WCount*
 // stands for no blocking side) and compares candidates by cross-
 // multiplication, so it divides once, for its own winner, instead of once
 // per side (an FP64 division is a long sequence on the FP64 pipe).
+// The sign tests read the sign bit on the integer pipe (an FP64 compare
+// costs as much as an FMA here): -0 and negative NaNs pass them but then
+// fail the comparison, as they fail the FP64 test.
 __device__ double wmax_step(const WCtx& C, const double* dlam, const double* dt) {
   const Batch& B = *C.B;
   double num = 1.0, den = 0.0;
   #pragma unroll 4
   for (int i = C.side0 + C.lane; i < C.side0 + C.nside; i += 32) {
     const double dl = dlam[i], dd = dt[i];
-    if (dl < 0.0) {
+    if (__double_as_longlong(dl) < 0) {
       const double a = B.lam[i];
       if (a * den < num * -dl) {
         num = a;
         den = -dl;
       }
     }
-    if (dd < 0.0) {
+    if (__double_as_longlong(dd) < 0) {
       const double a = B.t[i];
       if (a * den < num * -dd) {
         num = a;
@@ -945,7 +1202,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
   };
 
   if (kind == (int)LaunchKind::Residuals) {
-    const WNorms r = wresiduals(C);
+    const WNorms r = wresiduals<T>(C);
     if (lane == 0) {
       stats->res[0] = r.g;
       stats->res[1] = r.b;
@@ -956,7 +1213,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
     continue;
   }
   if (kind == (int)LaunchKind::NewtonStep) {
-    wresiduals(C);
+    wresiduals<T>(C);
     #pragma unroll 4
     for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32)
       B.rm[i] = B.lam[i] * B.t[i] - (B.lam[i] != 0.0 ? sigma_mu : 0.0);
@@ -1049,11 +1306,12 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
     cnt.res = stats->n_res;
   }
   int lifted_at = -1;  // iteration whose lambda, t were lifted after a lost FP64 pivot
+  const bool pos_min = arg.lam_min > 0.0 && arg.t_min > 0.0;  // the clamps can run on the integer pipe
   double alpha = 1.0;
   WNorms r{0, 0, 0, 0};
   const WDir d{B.dy, B.dpi, B.dlam, B.dt};
   while (true) {
-    r = wresiduals(C);
+    r = wresiduals<T>(C);
     ++cnt.res;
     if (!C.ok) {
       status = GQ_STATUS_TIMEOUT;
@@ -1141,7 +1399,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
       const double smu = sigma * r.mu;
       #pragma unroll 4
       for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32)
-        B.rm[i] = B.lam[i] != 0.0 ? B.lam[i] * B.t[i] + d.dlam[i] * d.dt[i] - smu : 0.0;
+        B.rm[i] = nonzero_bits(B.lam[i]) ? B.lam[i] * B.t[i] + d.dlam[i] * d.dt[i] - smu : 0.0;
       __syncwarp();
       double ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
       double amax = -1.0;  // step to the boundary of the current direction, once known
@@ -1152,7 +1410,7 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
         if (mu_c > arg.corr_k * mu_aff) {
           #pragma unroll 4
           for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32)
-            B.rm[i] = B.lam[i] != 0.0 ? B.lam[i] * B.t[i] - smu : 0.0;
+            B.rm[i] = nonzero_bits(B.lam[i]) ? B.lam[i] * B.t[i] - smu : 0.0;
           __syncwarp();
           ratio = wnewton<T>(C, d, ir, arg.ir_tol, &cnt);
           amax = -1.0;
@@ -1194,11 +1452,21 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
     for (int i = C.v0 + lane; i < C.v1; i += 32) B.y[i] += alpha * d.dy[i];
     #pragma unroll 4
     for (int i = C.e0 + lane; i < C.e1; i += 32) B.pi[i] += alpha * d.dpi[i];
-    #pragma unroll 4
-    for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) {
-      if (B.lam[i] != 0.0 || d.dlam[i] != 0.0) {
-        B.lam[i] = fmax(B.lam[i] + alpha * d.dlam[i], arg.lam_min);
-        B.t[i] = fmax(B.t[i] + alpha * d.dt[i], arg.t_min);
+    if (pos_min) {
+      #pragma unroll 4
+      for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) {
+        if (nonzero_bits(B.lam[i]) || nonzero_bits(d.dlam[i])) {
+          B.lam[i] = fmax_pos_bits(B.lam[i] + alpha * d.dlam[i], arg.lam_min);
+          B.t[i] = fmax_pos_bits(B.t[i] + alpha * d.dt[i], arg.t_min);
+        }
+      }
+    } else {
+      #pragma unroll 4
+      for (int i = C.side0 + lane; i < C.side0 + C.nside; i += 32) {
+        if (B.lam[i] != 0.0 || d.dlam[i] != 0.0) {
+          B.lam[i] = fmax(B.lam[i] + alpha * d.dlam[i], arg.lam_min);
+          B.t[i] = fmax(B.t[i] + alpha * d.dt[i], arg.t_min);
+        }
       }
     }
     __syncwarp();
@@ -1221,17 +1489,31 @@ __global__ void __maxnreg__(200) warp_ipm_kernel(const __grid_constant__ Batch B
   }  // next QP
 }
 
-// FP32 mirror of the stage data blocks: values converted, box indices copied
+// FP32 mirror of the stage data blocks: values rounded to FP32 (data32) and
+// the FP32 rounding of what that leaves (data32lo), so that hi + lo carries a
+// value to about 48 bits; box indices copied into both
 __global__ void mirror_kernel(const __grid_constant__ Batch B) {
   for (int sl = blockIdx.x; sl < B.nslots; sl += gridDim.x) {
     const StageDesc s = B.st[B.slots[sl]];
     const StageData L = wlay(s);
     const double* src = B.data + s.data;
     float* dst = B.data32 + s.data;
-    for (int64_t i = threadIdx.x; i < L.box; i += blockDim.x) dst[i] = (float)src[i];
+    float* dlo = B.data32lo + s.data;
+    for (int64_t i = threadIdx.x; i < L.box; i += blockDim.x) {
+      const double v = src[i];
+      const float h = (float)v;
+      dst[i] = h;
+      // v - h is exact in FP64; an infinite value (or one beyond the FP32
+      // range) leaves 0
+      dlo[i] = isfinite(h) ? (float)(v - (double)h) : 0.0f;
+    }
     const int32_t* si = reinterpret_cast<const int32_t*>(src + L.box);
     int32_t* di = reinterpret_cast<int32_t*>(dst + L.box);
-    for (int i = threadIdx.x; i < L.nint; i += blockDim.x) di[i] = si[i];
+    int32_t* dli = reinterpret_cast<int32_t*>(dlo + L.box);
+    for (int i = threadIdx.x; i < L.nint; i += blockDim.x) {
+      di[i] = si[i];
+      dli[i] = si[i];
+    }
   }
 }
 
