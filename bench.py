@@ -3,8 +3,9 @@
 Workload (one "step"): the mass-spring chain of Sec. 5.1 with 8 masses
 (nx = 16, nu = 7), N = 30, Q = I, R = I, |u| <= 0.5, |x| <= 4; a batch of
 1024 QPs that differ only in x0 ~ U[-1, 1]^16, each solved to KKT residual
-1e-8 by the mixed-precision IPM (FP32 Riccati factor/solve, FP64 residuals,
-refinement, step length and duality measure) in one kernel launch.
+1e-8 by the mixed-precision IPM (FP32 Riccati factor/solve; residual
+mat-vecs in double-float on the FP32 pipe, about 48 bits; FP64 refinement
+updates, recovery, step length and duality measure) in one kernel launch.
 
 Prints one JSON line: the metric, its end-to-end counterpart through the C
 ABI with host buffers, the roofline of the timed kernel (algorithmic flops of
@@ -90,29 +91,58 @@ def measure_peaks(stream_ptr) -> None:
         PEAKS.update(fp32=f32.value, fp64=f64.value, source="measured (FMA probe, gq_probe_fma_rate)")
 
 
+# FP32 instructions per double-float multiply-add (the kernel's df_acc: three
+# FMAs, one multiply and eight adds), against one FP32 FMA for the same two
+# algorithmic flops: double-float work runs at 1/12 of the FP32 flop rate
+DF_COST = 12.0
+
+
+def t_min_of(f32, f64, fdf):
+    """Shortest time of the work at the measured ALU peaks, each class on the
+    unit that executes it."""
+    return f32 / PEAKS["fp32"] + f64 / PEAKS["fp64"] + fdf * DF_COST / PEAKS["fp32"]
+
+
 def alu_roofline(qps, stats, seconds):
     """Achieved algorithmic flop rates of one batch solve and their fraction
     of the flop-mix-weighted ALU peak (FP32 lanes for the FP32 work, the FP64
-    rate for the FP64 work)."""
-    f32, f64 = work_split(qps, stats)
-    t_min = f32 / PEAKS["fp32"] + f64 / PEAKS["fp64"]
+    rate for the FP64 work, FP32 lanes / DF_COST for the double-float work)."""
+    f32, f64, fdf = work_split(qps, stats)
+    t_min = t_min_of(f32, f64, fdf)
     return {"fp32_tflops": f32 / seconds / 1e12, "fp64_tflops": f64 / seconds / 1e12,
+            "df_tflops": fdf / seconds / 1e12,
             "fp32_frac_of_peak": f32 / seconds / PEAKS["fp32"], "fp64_frac_of_peak": f64 / seconds / PEAKS["fp64"],
             "frac_of_mix_peak": t_min / seconds if t_min > 0 else None}
 
 
+def in_warp_kernel(qp) -> bool:
+    """The default schedule's one-warp bucket: every stage with nu + nx <= 32
+    and nx <= 32, no slacks."""
+    return (max(qp.nx[n] + qp.nu[n] for n in range(qp.N + 1)) <= 32 and max(qp.nx) <= 32
+            and all(qp.ns(n) == 0 for n in range(qp.N + 1)))
+
+
 def work_split(qps, stats):
-    """Algorithmic flops of one batch solve split by arithmetic type."""
-    f32 = f64 = 0.0
+    """Algorithmic flops of one batch solve split by arithmetic type: FP32
+    (factorisations and solves with the FP32 factor), FP64 (with the FP64
+    factor, and the block kernel's residuals) and double-float (the residuals
+    of the one-warp kernel's FP32 iterations)."""
+    f32 = f64 = fdf = 0.0
     for qp, st in zip(qps, stats):
         f, s, r = qp_flops(qp)
         nf = int(st["n_fact"])
         nf64 = int(st["n_fact64"])
         frac64 = nf64 / nf if nf else 0.0
         ns = int(st["n_solve"])
-        f64 += nf64 * f + ns * s * frac64 + int(st["n_res"]) * r
+        nr = int(st["n_res"])
+        f64 += nf64 * f + ns * s * frac64
         f32 += (nf - nf64) * f + ns * s * (1.0 - frac64)
-    return f32, f64
+        if in_warp_kernel(qp):
+            fdf += nr * r * (1.0 - frac64)
+            f64 += nr * r * frac64
+        else:
+            f64 += nr * r
+    return f32, f64, fdf
 
 
 # ----------------------------------------------------------------------------
@@ -415,7 +445,7 @@ def batch_run(qps, dev, precision: int, reps: int = 2, mode: int = 0, warp_max_n
     from paper_2003_02547_gb300.batch import QpBatch
     b = QpBatch(qps, device=dev)
     if warp_max_nv is not None:
-        b.set_schedule(warp_max_nv, 256)
+        b.set_schedule(warp_max_nv)
     arg = gq.default_arg(mode, precision)
     b.upload()
     b.solve(arg)
@@ -586,11 +616,14 @@ def main():
     p99 = float(np.percentile(step_sorted, 99))
 
     # ---------------- roofline of the IPM kernel ----------------
-    f32, f64 = work_split(qps, st)
+    f32, f64, fdf = work_split(qps, st)
     t_kernel = mean_ms * 1e-3
-    t_min = f32 / PEAKS["fp32"] + f64 / PEAKS["fp64"]
-    achieved = (f32 + f64) / t_kernel
-    peak_eff = (f32 + f64) / t_min if t_min > 0 else float("nan")
+    t_min = t_min_of(f32, f64, fdf)
+    achieved = (f32 + f64 + fdf) / t_kernel
+    peak_eff = (f32 + f64 + fdf) / t_min if t_min > 0 else float("nan")
+    # the same flops with the residual mat-vecs counted at the FP64 rate (the
+    # bound of an FP64 residual, the precision they stand in for)
+    t_min64 = f32 / PEAKS["fp32"] + (f64 + fdf) / PEAKS["fp64"]
 
     # ---------------- e2e through the C ABI with host buffers ----------------
     for _ in range(2):
@@ -734,9 +767,12 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_eff / 1e12, "unit": "TFLOP/s",
                          "frac": achieved / peak_eff if peak_eff == peak_eff else None, "traffic": captured_traffic(),
                          "kernel": "warp_ipm_kernel<float>", "flops_f32": f32, "flops_f64": f64,
+                         "flops_df": fdf,
                          "peak_fp32_tflops": PEAKS["fp32"] / 1e12, "peak_fp64_tflops": PEAKS["fp64"] / 1e12,
+                         "frac_residuals_at_fp64_rate": t_min64 / t_kernel,
                          "peak_note": f"FP32 and FP64 FMA peaks {PEAKS['source']} (nominal 80.5 and 1.25 TF); "
-                                      "peak = flop-mix-weighted"},
+                                      f"peak = flop-mix-weighted, each class on the unit that runs it (double-float "
+                                      f"residual mat-vecs at 1/{DF_COST:g} of the FP32 rate)"},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(b.sizes.in_bytes),
                     "d2h_bytes_per_step": int(b.sizes.sol_bytes), "converged": e2e_ok},
             "batched_fp64_gpu": {"value": batched_fp64, "unit": UNIT, "ms": statistics.mean(f64_ms),

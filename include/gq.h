@@ -331,7 +331,11 @@ typedef struct gq_schedule {
                               one per warp (0..32; 0: every QP in the block kernel);
                               QPs with soft constraints always run in the block
                               kernel                                                   */
-    int32_t block_threads; /* threads per block of the block kernel: 64, 128 or 256    */
+    int32_t block_threads; /* threads per block of the block kernel: 64, 128 or 256;
+                              0 (default): automatic, 128 when every block-bucket
+                              stage has nu + nx <= 96, else 256 (measured: more QPs
+                              per SM pay for small stages, more threads per QP for
+                              large ones)                                              */
     int32_t warp_qps;      /* out: QPs in the warp bucket                             */
     int32_t block_qps;     /* out: QPs in the block bucket                            */
     int32_t tensor_cores;  /* FP32 factors of large stages (128 <= nu + nx <= 256,
@@ -345,7 +349,8 @@ typedef struct gq_schedule {
                               products                                                  */
 } gq_schedule;
 
-/* Defaults: warp_max_nv 32, block_threads 256, tensor_cores 1 (automatic). */
+/* Defaults: warp_max_nv 32, block_threads 0 (automatic), tensor_cores 1
+ * (automatic). */
 GQ_API int gq_get_schedule(const gq_batch* b, gq_schedule* out);
 
 /* Re-plans the buckets (host handle and host "in" staging); gq_upload before

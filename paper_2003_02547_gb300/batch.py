@@ -306,7 +306,7 @@ class QpBatch:
         gq.check(self.lib.gq_get_schedule(self.h, ctypes.byref(sch)))
         return sch
 
-    def set_schedule(self, warp_max_nv: int, block_threads: int = 256, tensor_cores: int = 1) -> None:
+    def set_schedule(self, warp_max_nv: int, block_threads: int = 0, tensor_cores: int = 1) -> None:
         sch = gq.Schedule(warp_max_nv, block_threads, 0, 0, tensor_cores)
         gq.check(self.lib.gq_set_schedule(self.h, ctypes.byref(sch)))
 

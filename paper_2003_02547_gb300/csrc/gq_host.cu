@@ -188,6 +188,9 @@ namespace {
 
 // Shape of the QPs at positions [lo, hi) of the order array (all QPs when
 // `all`, whatever the order).
+// largest nu + nx of the block bucket for which the automatic block size is 128
+constexpr int kAutoThreadsNv = 96;
+
 Shape bucket_shape(const gq_batch* b, int lo, int hi, bool all) {
   Shape sh;
   std::memset(&sh, 0, sizeof(sh));
@@ -233,7 +236,11 @@ void plan_buckets(gq_batch* b) {
   b->shape_w = bucket_shape(b, 0, nw, false);
   b->shape_b = bucket_shape(b, nw, nqp, false);
   if (nqp > nw) b->shape_b.mat_global = 1;
-  b->shape_b.threads = b->block_threads;
+  // automatic block size (0): 128 threads (four QPs per SM) when the block
+  // bucket's stages have nu + nx <= 96, else 256 (measured: ragged batch
+  // 1.17x mixed, 1.26x FP64 at 128 threads; large stages of nu + nx = 192
+  // 1.6x slower at 128)
+  b->shape_b.threads = b->block_threads > 0 ? b->block_threads : (b->shape_b.nvmax <= kAutoThreadsNv ? 128 : 256);
   b->shape_b.tc_off = b->tensor_cores ? 0 : 1;
 }
 
@@ -367,7 +374,7 @@ int gq_batch_create_soft(int nqp, const int* dims, size_t dims_len, const int* s
     return fail(GQ_ERR_DIMS, "batch too large for 32-bit vector offsets");
 
   b->warp_max_nv = kWarpMaxNv;
-  b->block_threads = 256;
+  b->block_threads = 0;
   b->tensor_cores = 1;
   plan_buckets(b);
   // the block kernel keeps its stage matrices in a per-QP slice of a global
@@ -917,7 +924,7 @@ static cudaError_t launch_all(gq_batch* b, const Batch& k, const gq_ipm_arg& arg
   // block-kernel variant: slack elimination, tensor-core products of large
   // FP32 stages, or neither
   bool tc = !b->soft_block && tc_shape(b->shape_b) && arg.precision == GQ_PREC_MIXED &&
-            (b->block_threads == 256);
+            (b->shape_b.threads == 256);
   if (tc && b->tensor_cores == 1) {
     // automatic: only while the block bucket leaves at least every other SM
     // idle (measured on the large-stage batch: 1.5 % faster at 76 QPs on 152
@@ -982,8 +989,8 @@ int gq_set_schedule(gq_batch* b, const gq_schedule* sch) {
   if (sch == nullptr) return fail(GQ_ERR_ARG, "schedule is NULL");
   if (sch->warp_max_nv < 0 || sch->warp_max_nv > kWarpMaxNv)
     return fail(GQ_ERR_ARG, "warp_max_nv must be in 0..%d", kWarpMaxNv);
-  if (sch->block_threads != 64 && sch->block_threads != 128 && sch->block_threads != 256)
-    return fail(GQ_ERR_ARG, "block_threads must be 64, 128 or 256");
+  if (sch->block_threads != 0 && sch->block_threads != 64 && sch->block_threads != 128 && sch->block_threads != 256)
+    return fail(GQ_ERR_ARG, "block_threads must be 0 (automatic), 64, 128 or 256");
   if (sch->tensor_cores < 0 || sch->tensor_cores > 2) return fail(GQ_ERR_ARG, "tensor_cores must be 0, 1 or 2");
   b->warp_max_nv = sch->warp_max_nv;
   b->block_threads = sch->block_threads;
@@ -1022,7 +1029,7 @@ int gq_autotune(gq_batch* b, const gq_ipm_arg* arg, void* stream, int reps, gq_s
     if (rc) break;
     // a candidate that runs the same kernels as an earlier one is skipped
     // (block size without block-bucket QPs; tensor cores where no stage uses them)
-    const int thr = b->nqp > b->nwarp ? b->block_threads : 0;
+    const int thr = b->nqp > b->nwarp ? b->shape_b.threads : 0;
     const int tcu = (b->nqp > b->nwarp && thr == 256 && arg->precision == GQ_PREC_MIXED) ? c.tensor_cores : 0;
     bool dup = false;
     for (int k = 0; k < nseen; ++k)

@@ -1049,11 +1049,17 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
         }
       }
     }
+    // rb_n in the factor's precision, converted once (a conversion from FP64
+    // costs as much as an FP64 FMA on this GPU); phi is free until formed below
+    Tf* rbf = phi;
+    if (n < C.N)
+      for (int j = tid; j < nx1; j += NT) rbf[j] = (Tf)rb[s.eq + j];
+    __syncthreads();
     if (n < C.N && !C.classical) {
       // va = L_{n+1}' rb_n
       rows_dot<Tf>(
           nx1, [&](int k) { return k; }, [&](int) { return nx1; },
-          [&](int k, int j) { return sL[j * nx1 + k] * (Tf)rb[s.eq + j]; }, [&](int k, Tf v) { va[k] = v; });
+          [&](int k, int j) { return sL[j * nx1 + k] * rbf[j]; }, [&](int k, Tf v) { va[k] = v; });
     }
     __syncthreads();
     if (n < C.N) {
@@ -1061,7 +1067,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
         // vb = P_{n+1} rb_n + p_{n+1}
         rows_dot<Tf>(
             nx1, [&](int) { return 0; }, [&](int) { return nx1; },
-            [&](int k, int j) { return sL[k * nx1 + j] * (Tf)rb[s.eq + j]; }, [&](int k, Tf v) { vb[k] = pn1[k] + v; });
+            [&](int k, int j) { return sL[k * nx1 + j] * rbf[j]; }, [&](int k, Tf v) { vb[k] = pn1[k] + v; });
       } else {
         // vb = L_{n+1} va + p_{n+1}
         rows_dot<Tf>(
@@ -1121,20 +1127,25 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     const int nv = s.nx + s.nu, nx1 = s.nx1, nb = s.nbu + s.nbx, nc = nb + s.ng;
     const int ne = elim_size(s, n), nk = nv - ne;
     double* yn = dy + s.var;
+    // x_n (and below y_n) in the factor's precision, converted once into the
+    // backward sweep's scratch (vb, phi are free here)
+    Tf* xf = vb;
+    Tf* yf = phi;
+    for (int j = tid; j < nk; j += NT) xf[j] = (Tf)yn[ne + j];
+    __syncthreads();
     if (n > 0) {
-      const double* xn = yn + ne;
       const int eqp = C.st[n - 1].eq;
       if (C.classical) {
         // pi_n = P_n x_n + p_n, P_n stored in the lower kk block
         rows_dot<Tf>(
             nk, [&](int) { return 0; }, [&](int) { return nk; },
-            [&](int k, int j) { return F[(ne + max(k, j)) * nv + ne + min(k, j)] * (Tf)xn[j]; },
+            [&](int k, int j) { return F[(ne + max(k, j)) * nv + ne + min(k, j)] * xf[j]; },
             [&](int k, Tf v) { dpi[eqp + k] = (double)((Tf)lp[s.var + ne + k] + v); });
       } else {
         // pi_n = L_n (L_n' x_n) + p_n,  L_n = L_kk of this stage
         rows_dot<Tf>(
             nk, [&](int k) { return k; }, [&](int) { return nk; },
-            [&](int k, int j) { return F[(ne + j) * nv + ne + k] * (Tf)xn[j]; }, [&](int k, Tf v) { va[k] = v; });
+            [&](int k, int j) { return F[(ne + j) * nv + ne + k] * xf[j]; }, [&](int k, Tf v) { va[k] = v; });
         __syncthreads();
         rows_dot<Tf>(
             nk, [&](int) { return 0; }, [&](int k) { return k + 1; },
@@ -1146,7 +1157,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     // va = l + L_ke' x_n
     rows_dot<Tf>(
         ne, [&](int) { return 0; }, [&](int) { return nk; },
-        [&](int j, int i) { return F[(ne + i) * nv + j] * (Tf)yn[ne + i]; },
+        [&](int j, int i) { return F[(ne + i) * nv + j] * xf[i]; },
         [&](int j, Tf v) { va[j] = (Tf)lp[s.var + j] + v; });
     __syncthreads();
     // y_e = -X' va
@@ -1156,10 +1167,12 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     __syncthreads();
     if (n < C.N) {
       // x_{n+1} = [B A] y_n + rb_n
+      for (int i = tid; i < nv; i += NT) yf[i] = (Tf)yn[i];
+      __syncthreads();
       double* x1 = dy + C.st[n + 1].var + C.st[n + 1].nu;
       rows_dot<Tf>(
           nx1, [&](int) { return 0; }, [&](int) { return nv; },
-          [&](int k, int i) { return (Tf)D[L.BAt + (int64_t)i * L.ldb + k] * (Tf)yn[i]; },
+          [&](int k, int i) { return (Tf)D[L.BAt + (int64_t)i * L.ldb + k] * yf[i]; },
           [&](int k, Tf v) { x1[k] = (double)((Tf)rb[s.eq + k] + v); });
     }
     // dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt) on active sides

@@ -271,7 +271,7 @@ def test_schedule_replans_buckets(gqmod):
     qps = [W.small_random_qp(0), W.ragged_random_qp(0), W.mass_spring_qp(0)]
     b = QpBatch(qps, device=None)
     sch = b.schedule()
-    assert (sch.warp_max_nv, sch.block_threads) == (32, 256)
+    assert (sch.warp_max_nv, sch.block_threads) == (32, 0)
     nw = sum(max(q.nx[n] + q.nu[n] for n in range(q.N + 1)) <= 32 and max(q.nx) <= 32 for q in qps)
     assert (sch.warp_qps, sch.block_qps) == (nw, len(qps) - nw)
     b.set_schedule(0, 128)
