@@ -103,11 +103,11 @@ def t_min_of(f32, f64, fdf):
     return f32 / PEAKS["fp32"] + f64 / PEAKS["fp64"] + fdf * DF_COST / PEAKS["fp32"]
 
 
-def alu_roofline(qps, stats, seconds):
+def alu_roofline(qps, stats, seconds, warp_max_nv: int = 32):
     """Achieved algorithmic flop rates of one batch solve and their fraction
     of the flop-mix-weighted ALU peak (FP32 lanes for the FP32 work, the FP64
     rate for the FP64 work, FP32 lanes / DF_COST for the double-float work)."""
-    f32, f64, fdf = work_split(qps, stats)
+    f32, f64, fdf = work_split(qps, stats, warp_max_nv)
     t_min = t_min_of(f32, f64, fdf)
     return {"fp32_tflops": f32 / seconds / 1e12, "fp64_tflops": f64 / seconds / 1e12,
             "df_tflops": fdf / seconds / 1e12,
@@ -115,14 +115,14 @@ def alu_roofline(qps, stats, seconds):
             "frac_of_mix_peak": t_min / seconds if t_min > 0 else None}
 
 
-def in_warp_kernel(qp) -> bool:
-    """The default schedule's one-warp bucket: every stage with nu + nx <= 32
-    and nx <= 32, no slacks."""
-    return (max(qp.nx[n] + qp.nu[n] for n in range(qp.N + 1)) <= 32 and max(qp.nx) <= 32
+def in_warp_kernel(qp, warp_max_nv: int = 32) -> bool:
+    """The schedule's one-warp bucket: every stage with nu + nx and nx at
+    most warp_max_nv, no slacks."""
+    return (max(qp.nx[n] + qp.nu[n] for n in range(qp.N + 1)) <= warp_max_nv and max(qp.nx) <= warp_max_nv
             and all(qp.ns(n) == 0 for n in range(qp.N + 1)))
 
 
-def work_split(qps, stats):
+def work_split(qps, stats, warp_max_nv: int = 32):
     """Algorithmic flops of one batch solve split by arithmetic type: FP32
     (factorisations and solves with the FP32 factor), FP64 (with the FP64
     factor, and the block kernel's residuals) and double-float (the residuals
@@ -137,7 +137,7 @@ def work_split(qps, stats):
         nr = int(st["n_res"])
         f64 += nf64 * f + ns * s * frac64
         f32 += (nf - nf64) * f + ns * s * (1.0 - frac64)
-        if in_warp_kernel(qp):
+        if in_warp_kernel(qp, warp_max_nv):
             fdf += nr * r * (1.0 - frac64)
             f64 += nr * r * frac64
         else:
@@ -464,7 +464,7 @@ def batch_run(qps, dev, precision: int, reps: int = 2, mode: int = 0, warp_max_n
     out = {"value": len(qps) / (min(ms) * 1e-3), "unit": UNIT, "ms": min(ms), "qps": len(qps),
            "converged": int(np.sum(st["status"] == 0)), "iters_mean": float(np.mean(st["iters"])),
            "fp64_fallback_qps": int(np.sum(st["flags"] & gq.FLAG_FP64_FALLBACK != 0)),
-           "alu": alu_roofline(qps, st, min(ms) * 1e-3)}
+           "alu": alu_roofline(qps, st, min(ms) * 1e-3, 32 if warp_max_nv is None else warp_max_nv)}
     if mode == gq.MODE_BALANCE:
         out["array_qr_qps"] = int(np.sum(st["flags"] & gq.FLAG_ARRAY_QR != 0))
     del b
@@ -476,7 +476,7 @@ def batch_run(qps, dev, precision: int, reps: int = 2, mode: int = 0, warp_max_n
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; summary in
 # profiles/).  It is reported only while the kernel sources hash to the
 # value recorded with the capture; after any change it reads null.
-TRAFFIC_CAPTURE = {"sha256": "66bfa1de21b80a5a3cccf9ebc699569c40834b6944bd5f0ec578cae7f36a76f5", "bytes": 5858079232}
+TRAFFIC_CAPTURE = {"sha256": "7e4700c08c490244c2bdc737b381803939d3e12a1bcc1a4c8da4eb9d52ca5616", "bytes": 5584384512}
 KERNEL_SOURCES = ["gq_warp.cu", "gq_device.h", "gq_internal.h", "gq_launch.h", "gq_mma.h"]
 
 

@@ -333,9 +333,11 @@ typedef struct gq_schedule {
                               kernel                                                   */
     int32_t block_threads; /* threads per block of the block kernel: 64, 128 or 256;
                               0 (default): automatic, 128 when every block-bucket
-                              stage has nu + nx <= 96, else 256 (measured: more QPs
-                              per SM pay for small stages, more threads per QP for
-                              large ones)                                              */
+                              stage has nu + nx <= 96 and the bucket holds more
+                              QPs than two per SM, else 256 (measured: more QPs per
+                              SM pay for full buckets of small stages, more threads
+                              per QP for large stages and for buckets that fit the
+                              GPU at once)                                             */
     int32_t warp_qps;      /* out: QPs in the warp bucket                             */
     int32_t block_qps;     /* out: QPs in the block bucket                            */
     int32_t tensor_cores;  /* FP32 factors of large stages (128 <= nu + nx <= 256,

@@ -191,6 +191,18 @@ namespace {
 // largest nu + nx of the block bucket for which the automatic block size is 128
 constexpr int kAutoThreadsNv = 96;
 
+// SMs of the current device; 0 without one (the automatic block size then
+// stays at 256)
+int device_sms() {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nsm;
+}
+
 Shape bucket_shape(const gq_batch* b, int lo, int hi, bool all) {
   Shape sh;
   std::memset(&sh, 0, sizeof(sh));
@@ -237,10 +249,15 @@ void plan_buckets(gq_batch* b) {
   b->shape_b = bucket_shape(b, nw, nqp, false);
   if (nqp > nw) b->shape_b.mat_global = 1;
   // automatic block size (0): 128 threads (four QPs per SM) when the block
-  // bucket's stages have nu + nx <= 96, else 256 (measured: ragged batch
-  // 1.17x mixed, 1.26x FP64 at 128 threads; large stages of nu + nx = 192
-  // 1.6x slower at 128)
-  b->shape_b.threads = b->block_threads > 0 ? b->block_threads : (b->shape_b.nvmax <= kAutoThreadsNv ? 128 : 256);
+  // bucket's stages have nu + nx <= 96 and it holds more QPs than two per SM
+  // take at once, else 256 (measured: ragged batch of 4096 QPs 1.17x mixed,
+  // 1.26x FP64 at 128 threads; large stages of nu + nx = 192 1.6x slower at
+  // 128; a bucket that fits the GPU at 256 threads finishes sooner with them,
+  // as the server's micro-batches do)
+  const int nsm = b->block_threads > 0 ? 0 : device_sms();
+  b->shape_b.threads = b->block_threads > 0 ? b->block_threads
+                       : (b->shape_b.nvmax <= kAutoThreadsNv && nsm > 0 && nqp - nw > 2 * nsm) ? 128
+                                                                                               : 256;
   b->shape_b.tc_off = b->tensor_cores ? 0 : 1;
 }
 
