@@ -936,7 +936,10 @@ static int make_kernel_batch(const gq_batch* b, Batch* k) {
 static cudaError_t launch_all(gq_batch* b, const Batch& k, const gq_ipm_arg& arg, cudaStream_t st, LaunchKind kind,
                               double sigma_mu, const DirOut* out) {
   const int32_t* ord = k.order;
-  cudaError_t e = launch_warp_ipm(k, b->shape_w, arg, st, kind, sigma_mu, out, ord, b->nwarp);
+  cudaError_t e = cudaSuccess;
+  if (arg.precision == GQ_PREC_MIXED && kind != LaunchKind::Residuals) e = launch_mirror(k, st);
+  if (e != cudaSuccess) return e;
+  e = launch_warp_ipm(k, b->shape_w, arg, st, kind, sigma_mu, out, ord, b->nwarp);
   if (e != cudaSuccess) return e;
   // block-kernel variant: slack elimination, tensor-core products of large
   // FP32 stages, or neither

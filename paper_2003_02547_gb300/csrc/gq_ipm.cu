@@ -289,15 +289,21 @@ __device__ __forceinline__ double cons_value(const StageDesc& s, const StageData
 // ---------------------------------------------------------------------------
 // stage sweeps over the bulk-copy ring
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void ring_issue(Ctx& C, int n, int b, int fac_elem) {
+// stage data of the precision data_elem selects: the FP64 block (8) or its
+// FP32 mirror (4, the same element layout)
+__device__ __forceinline__ const void* stage_data(const Batch& B, const StageDesc& s, int data_elem) {
+  return data_elem == 4 ? static_cast<const void*>(B.data32 + s.data) : static_cast<const void*>(B.data + s.data);
+}
+
+__device__ __forceinline__ void ring_issue(Ctx& C, int n, int b, int fac_elem, int data_elem) {
   const Batch& B = *C.B;
   const StageDesc& s = C.st[n];
   if (threadIdx.x == 0) {
-    const uint32_t dbytes = (uint32_t)(lay(s).size * 8);
+    const uint32_t dbytes = (uint32_t)(lay(s).size * data_elem);
     const uint32_t fbytes = fac_elem ? (uint32_t)(fac_block_elems(s.nx + s.nu) * fac_elem) : 0u;
     fence_async_shared();
     mbar_arrive_expect_tx(&C.ring.bar[b], dbytes + fbytes);
-    bulk_g2s(C.ring.buf[b], B.data + s.data, dbytes, &C.ring.bar[b]);
+    bulk_g2s(C.ring.buf[b], stage_data(B, s, data_elem), dbytes, &C.ring.bar[b]);
     if (fbytes)
       bulk_g2s(C.ring.buf[b] + C.ring.fac_off, static_cast<const unsigned char*>(B.fac) + s.fac * 8, fbytes,
                &C.ring.bar[b]);
@@ -312,11 +318,12 @@ __device__ __forceinline__ void ring_wait(Ctx& C, int b) {
 }
 
 // Calls f(n, D, F) for every stage, forward or backward.  D is the stage data
-// block and F (when fac_elem > 0) the stage factor block, both in shared
-// memory when the ring is on.  f may synchronise internally; the sweep adds a
-// barrier after each stage before its buffer is refilled.
+// block (FP64, or with data_elem 4 its FP32 mirror: the callee reads it as
+// its factor type) and F (when fac_elem > 0) the stage factor block, both in
+// shared memory when the ring is on.  f may synchronise internally; the sweep
+// adds a barrier after each stage before its buffer is refilled.
 template <class F>
-__device__ void sweep(Ctx& C, bool backward, int fac_elem, F f) {
+__device__ void sweep(Ctx& C, bool backward, int fac_elem, F f, int data_elem = 8) {
   const Batch& B = *C.B;
   const int N = C.N;
   if (!C.ring.staged) {
@@ -324,15 +331,15 @@ __device__ void sweep(Ctx& C, bool backward, int fac_elem, F f) {
       const int n = backward ? N - k : k;
       const StageDesc& s = C.st[n];
       const unsigned char* fac = static_cast<const unsigned char*>(B.fac) + s.fac * 8;
-      f(n, B.data + s.data, static_cast<const void*>(fac));
+      f(n, static_cast<const double*>(stage_data(B, s, data_elem)), static_cast<const void*>(fac));
       __syncthreads();
     }
     return;
   }
-  ring_issue(C, backward ? N : 0, 0, fac_elem);
+  ring_issue(C, backward ? N : 0, 0, fac_elem, data_elem);
   for (int k = 0; k <= N; ++k) {
     const int n = backward ? N - k : k, b = k & 1;
-    if (k < N) ring_issue(C, backward ? n - 1 : n + 1, b ^ 1, fac_elem);
+    if (k < N) ring_issue(C, backward ? n - 1 : n + 1, b ^ 1, fac_elem, data_elem);
     ring_wait(C, b);
     f(n, reinterpret_cast<const double*>(C.ring.buf[b]), static_cast<const void*>(C.ring.buf[b] + C.ring.fac_off));
     __syncthreads();
@@ -519,7 +526,7 @@ __device__ __forceinline__ void tc_chunk_mma(Ctx& C, int t0, int t1, int brow, i
   tc::fence_after();
 }
 
-__device__ __noinline__ void tc_products(Ctx& C, int n, const double* D, const StageData& L, const StageDesc& s, float* sL,
+__device__ __noinline__ void tc_products(Ctx& C, int n, const float* D, const StageData& L, const StageDesc& s, float* sL,
                             float* sPhi, float* sMt, int ldP, const float* sw, const int32_t* bmap, double reg) {
   const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, w = tid >> 5;
   const int nv = s.nx + s.nu, nx1 = s.nx1, nb = s.nbu + s.nbx;
@@ -594,8 +601,9 @@ __device__ __noinline__ void tc_products(Ctx& C, int n, const double* D, const S
 
 #endif  // GQ_IPM_TC
 
+// D: the stage data in the factor's precision (the FP32 mirror for Tf = float)
 template <typename Tf>
-__device__ bool factor_stage(GQ_FCTX& C, int n, const double* D, double reg) {
+__device__ bool factor_stage(GQ_FCTX& C, int n, const Tf* D, double reg) {
   const Batch& B = *C.B;
   const int tid = threadIdx.x, NT = blockDim.x;
   const int ldP = block_ld(C.nvmax);
@@ -610,7 +618,8 @@ __device__ bool factor_stage(GQ_FCTX& C, int n, const double* D, double reg) {
   const int ne = elim_size(s, n), nk = nv - ne;
   const double* lm = B.lam + s.side;
   const double* tt = B.t + s.side;
-  const int32_t* bmap = box_idx(D, L) + nb;
+  const double* D64 = B.data + s.data;  // FP64 stage data (global) where exact values are needed
+  const int32_t* bmap = reinterpret_cast<const int32_t*>(D + L.box) + nb;
   // barrier weights W_lo + W_hi per constraint
   for (int c = tid; c < nc; c += NT) {
     double w = 0.0;
@@ -621,11 +630,11 @@ __device__ bool factor_stage(GQ_FCTX& C, int n, const double* D, double reg) {
   if (GQ_IPM_SOFT && s.ns > 0) {
     // relaxed constraints: their slacks eliminated into the weight (Sec. 2.2)
     __syncthreads();
-    const int32_t* sidx = soft::soft_sidx(box_idx(D, L), nb, nv);
+    const int32_t* sidx = soft::soft_sidx(box_idx(D64, L), nb, nv);
     for (int k = tid; k < s.ns; k += NT) {
       const int c = sidx[k];
       const soft::SoftSlot q = soft::soft_slot(s, nv, nc, k, c);
-      const soft::SoftElim e = soft::soft_elim(D, L, s.ns, k, q, D[L.lo + c] != -INFINITY, D[L.hi + c] != INFINITY,
+      const soft::SoftElim e = soft::soft_elim(D64, L, s.ns, k, q, D[L.lo + c] != -INFINITY, D[L.hi + c] != INFINITY,
                                                B.lam, B.t, nullptr, nullptr, nullptr);
       sw[c] = (Tf)soft::soft_weight(e);
     }
@@ -757,7 +766,7 @@ __device__ bool factor_stage(GQ_FCTX& C, int n, const double* D, double reg) {
       for (int t = tid; t < nI * nJ; t += NT) {
         const int I = t / nJ, J = t - I * nJ;
         Tf acc[kT][kT] = {};
-        const double* ba[kT];
+        const Tf* ba[kT];
   #pragma unroll
         for (int r = 0; r < kT; ++r) ba[r] = D + L.BAt + (int64_t)min(I * kT + r, nv - 1) * L.ldb;
         for (int k = C.classical ? 0 : J * kT; k < nx1; ++k) {
@@ -799,7 +808,7 @@ __device__ bool factor_stage(GQ_FCTX& C, int n, const double* D, double reg) {
         }
       }
       for (int g = 0; g < s.ng; ++g) {
-        const double* row = D + L.DC + (int64_t)g * nv;
+        const Tf* row = D + L.DC + (int64_t)g * nv;
         const Tf wg = sw[nb + g];
         Tf a[kT], bb[kT];
   #pragma unroll
@@ -990,7 +999,10 @@ __device__ bool factor_stage(GQ_FCTX& C, int n, const double* D, double reg) {
 template <typename Tf>
 __device__ bool factor(Ctx& C, double reg) {
   bool ok = true;
-  sweep(C, true, 0, [&](int n, const double* D, const void*) { ok = factor_stage<Tf>(C, n, D, reg) && ok; });
+  sweep(
+      C, true, 0,
+      [&](int n, const double* D, const void*) { ok = factor_stage<Tf>(C, n, reinterpret_cast<const Tf*>(D), reg) && ok; },
+      (int)sizeof(Tf));
   // factor blocks were written through the generic proxy; the solves read them
   // with bulk copies (async proxy)
   fence_async_global();
@@ -1018,14 +1030,18 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
   double* lp = B.lp;                 // per stage: l (ne entries) then p_n (nk entries)
   const int fe = (int)sizeof(Tf);
   double scale = 0.0;                // ||(gt, r_b)||inf of the reduced system
-  // backward sweep
-  sweep(C, true, fe, [&](int n, const double* D, const void* Fv) {
+  // backward sweep; D is the stage data in the factor's precision (the FP32
+  // mirror for Tf = float), D64 the FP64 data (global) where exact values
+  // are needed
+  sweep(C, true, fe, [&](int n, const double* Dv, const void* Fv) {
+    const Tf* D = reinterpret_cast<const Tf*>(Dv);
     const Tf* F = static_cast<const Tf*>(Fv);
     const StageDesc s = C.st[n];
     const StageData L = lay(s);
+    const double* D64 = B.data + s.data;
     const int nv = s.nx + s.nu, nx1 = s.nx1, nb = s.nbu + s.nbx, nc = nb + s.ng;
     const int ne = elim_size(s, n), nk = nv - ne;
-    const int32_t* bmap = box_idx(D, L) + nb;
+    const int32_t* bmap = reinterpret_cast<const int32_t*>(D + L.box) + nb;
     if (rd != nullptr) {
       const double* lm = B.lam + s.side;
       const double* tt = B.t + s.side;
@@ -1039,11 +1055,11 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
       if (GQ_IPM_SOFT && s.ns > 0) {
         // relaxed constraints: the eliminated slacks' gradient terms
         __syncthreads();
-        const int32_t* sidx = soft::soft_sidx(box_idx(D, L), nb, nv);
+        const int32_t* sidx = soft::soft_sidx(box_idx(D64, L), nb, nv);
         for (int k = tid; k < s.ns; k += NT) {
           const int c = sidx[k];
           const soft::SoftSlot q = soft::soft_slot(s, nv, nc, k, c);
-          const soft::SoftElim e = soft::soft_elim(D, L, s.ns, k, q, D[L.lo + c] != -INFINITY,
+          const soft::SoftElim e = soft::soft_elim(D64, L, s.ns, k, q, D[L.lo + c] != -INFINITY,
                                                    D[L.hi + c] != INFINITY, B.lam, B.t, g, rd, rm);
           vs[c] += soft::soft_grad(e);
         }
@@ -1085,7 +1101,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
           [&](int i, Tf v) {
             double gi = g[s.var + i];
             if (rd != nullptr) {
-              for (int gg = 0; gg < s.ng; ++gg) gi = fma(-D[L.DC + (int64_t)gg * nv + i], vs[nb + gg], gi);
+              for (int gg = 0; gg < s.ng; ++gg) gi = fma(-D64[L.DC + (int64_t)gg * nv + i], vs[nb + gg], gi);
               if (nb > 0 && bmap[i] >= 0) gi -= vs[bmap[i]];
             }
             scale = max_nan(scale, fabs(gi));
@@ -1117,13 +1133,15 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
       // L_n (lower, zeros above) or P_n (stored lower, used full)
       sL[i * nk + j] = C.classical ? F[(ne + max(i, j)) * nv + ne + min(i, j)] : F[(ne + i) * nv + ne + j];
     }
-  });
+  }, fe);
   // forward sweep: pi_n at the start of stage n (needs L_n), then y_n and
   // x_{n+1}, then dt, dlam of stage n
-  sweep(C, false, fe, [&](int n, const double* D, const void* Fv) {
+  sweep(C, false, fe, [&](int n, const double* Dv, const void* Fv) {
+    const Tf* D = reinterpret_cast<const Tf*>(Dv);
     const Tf* F = static_cast<const Tf*>(Fv);
     const StageDesc s = C.st[n];
     const StageData L = lay(s);
+    const double* D64 = B.data + s.data;
     const int nv = s.nx + s.nu, nx1 = s.nx1, nb = s.nbu + s.nbx, nc = nb + s.ng;
     const int ne = elim_size(s, n), nk = nv - ne;
     double* yn = dy + s.var;
@@ -1177,7 +1195,7 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
     }
     // dt = C dy - r_d, dlam = -T^{-1}(r_m + Lambda dt) on active sides
     for (int c = tid; c < nc; c += NT) {
-      const double v = cons_value(s, L, D, c, yn);
+      const double v = cons_value(s, L, D64, c, yn);
       const int il = s.side + c, iu = s.side + nc + c;
       const double dl = rd ? rd[il] : 0.0, du = rd ? rd[iu] : 0.0;
       const double ml = rm ? rm[il] : 0.0, mu = rm ? rm[iu] : 0.0;
@@ -1199,16 +1217,16 @@ __device__ double riccati_solve(Ctx& C, const double* g, const double* rd, const
       }
       if (GQ_IPM_SOFT && s.ns > 0) {
         // relaxed constraint: slack steps, then its sides' steps with them
-        const int k = soft::soft_smap(box_idx(D, L), nb, nv, s.ns)[c];
+        const int k = soft::soft_smap(box_idx(D64, L), nb, nv, s.ns)[c];
         if (k >= 0) {
           const soft::SoftSlot q = soft::soft_slot(s, nv, nc, k, c);
           const bool lo_on = D[L.lo + c] != -INFINITY, hi_on = D[L.hi + c] != INFINITY;
-          const soft::SoftElim e = soft::soft_elim(D, L, s.ns, k, q, lo_on, hi_on, B.lam, B.t, g, rd, rm);
+          const soft::SoftElim e = soft::soft_elim(D64, L, s.ns, k, q, lo_on, hi_on, B.lam, B.t, g, rd, rm);
           soft::soft_recover(e, q, lo_on, hi_on, v, B.lam, B.t, rd, rm, dy, dt, dlam);
         }
       }
     }
-  });
+  }, fe);
   return block_reduce(scale, C.red, OpMax());
 }
 

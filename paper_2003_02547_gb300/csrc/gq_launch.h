@@ -63,6 +63,10 @@ struct WarpPlan {
 WarpPlan warp_plan(const Batch& b, const Shape& sh, int elem);  // elem: factor element size
 cudaError_t launch_warp_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
                             LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count);
+// FP32 mirror of the stage data (values and their FP32 remainders), read by
+// both kernels' FP32 factorisations and solves and the one-warp kernel's
+// double-float residuals; launched before every mixed-precision launch pair
+cudaError_t launch_mirror(const Batch& b, cudaStream_t stream);
 
 constexpr size_t kMaxSmem = 227 * 1024;
 

@@ -1577,6 +1577,13 @@ static cudaError_t launch_one(const Batch& b, const Shape& sh, const gq_ipm_arg&
   return cudaGetLastError();
 }
 
+cudaError_t launch_mirror(const Batch& b, cudaStream_t stream) {
+  int grid = b.nslots < 4096 ? b.nslots : 4096;
+  if (grid < 1) grid = 1;
+  mirror_kernel<<<grid, 128, 0, stream>>>(b);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_warp_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& arg, cudaStream_t stream,
                             LaunchKind kind, double sigma_mu, const DirOut* out, const int32_t* order, int count) {
   if (count <= 0) return cudaSuccess;
@@ -1584,9 +1591,6 @@ cudaError_t launch_warp_ipm(const Batch& b, const Shape& sh, const gq_ipm_arg& a
   if (out) o = *out;
   if (arg.precision != GQ_PREC_MIXED || kind == LaunchKind::Residuals)
     return launch_one<double>(b, sh, arg, stream, kind, sigma_mu, o, order, count);
-  int grid = b.nslots < 4096 ? b.nslots : 4096;
-  if (grid < 1) grid = 1;
-  mirror_kernel<<<grid, 128, 0, stream>>>(b);
   cudaError_t e = launch_one<float>(b, sh, arg, stream, kind, sigma_mu, o, order, count);
   if (e != cudaSuccess || kind != LaunchKind::Solve || !arg.fp64_fallback) return e;
   // FP64 continuation of the QPs whose FP32 factors were not accurate enough
