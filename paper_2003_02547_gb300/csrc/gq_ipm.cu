@@ -1311,7 +1311,15 @@ __device__ double newton_dir(Ctx& C, const Dir& d, int ir, double ir_tol, Count*
 // ---------------------------------------------------------------------------
 // the kernel: one block per QP
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) ipm_kernel(const __grid_constant__ Batch B, const Shape sh,
+// The slack build is held to 128 registers (two 256-thread or four
+// 128-thread blocks per SM, as the other builds get from ptxas on their
+// own): left free, ptxas gave it 230 registers and it ran 1.4x slower.
+#if GQ_IPM_SOFT
+#define GQ_IPM_BOUNDS __launch_bounds__(256, 2)
+#else
+#define GQ_IPM_BOUNDS __launch_bounds__(256)
+#endif
+__global__ void GQ_IPM_BOUNDS ipm_kernel(const __grid_constant__ Batch B, const Shape sh,
                                                   const __grid_constant__ gq_ipm_arg arg, int kind,
                                                   double sigma_mu, const DirOut out, const int32_t* order) {
   extern __shared__ __align__(128) unsigned char smem[];
